@@ -1,0 +1,82 @@
+"""Stages (b) and (c): BRDF decoder B and implicit ray tracer I  (oracle, FP64).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Both are MLPs with "3 layers in total with hidden dimensions set to 64"
+(Sec. 4.1): y = W3 ReLU(W2 ReLU(W1 z + b1) + b2) + b3 (reading: biases
+present; they are zero in the synthetic scenes unless a test sets them).
+
+B (Sec. 3.2 and Sec. 3.3): z = f; the output vector is [n, a, r]
+(treated "as one concatenated output vector"), then n <- n / ||n||,
+a <- sigmoid(a), r <- 0.09 + 0.91 sigmoid(r).
+
+I (Sec. 3.2 and Sec. 3.3): z = [f, PE(w)] with PE(w) = [w, sin(2^k pi w),
+cos(2^k pi w)] for k = 0..3 (27 values; reading: the raw direction is
+included and the frequency count is 4); outputs v = sigmoid(z0) and
+t_hat = softplus(z1); the depth is min-max normalised between near and far
+and clamped to 1 (= far), so t = near + (far - near) * min(t_hat, 1).
+
+Pins (tests/test_oracle_mlp.py): the MLP against a numpy float64 matmul
+chain; sigmoid/softplus at known points; the positional encoding against
+its closed-form values at w = 0 and at the axes; the depth mapping at its
+end points.
+"""
+from __future__ import annotations
+
+import math
+from typing import List, Sequence, Tuple
+
+import torch
+
+Layers = Sequence[Tuple[torch.Tensor, torch.Tensor]]
+
+N_FREQ = 4
+PE_DIM = 3 + 2 * 3 * N_FREQ   # 27
+
+
+def as_layers(layers) -> List[Tuple[torch.Tensor, torch.Tensor]]:
+    """Convert (W, b) array pairs to float64 tensors."""
+    return [(torch.as_tensor(w, dtype=torch.float64), torch.as_tensor(b, dtype=torch.float64))
+            for w, b in layers]
+
+
+def mlp3(z: torch.Tensor, layers: Layers) -> torch.Tensor:
+    """Three linear layers with ReLU after the first two."""
+    (w1, b1), (w2, b2), (w3, b3) = layers
+    h1 = torch.relu(z @ w1.T + b1)
+    h2 = torch.relu(h1 @ w2.T + b2)
+    return h2 @ w3.T + b3
+
+
+def brdf_decoder(f: torch.Tensor, layers: Layers):
+    """a, r, n = B(f): albedo [.,3], roughness [.], unit normal [.,3]."""
+    y = mlp3(f, layers)
+    n = y[:, 0:3]
+    n = n / n.norm(dim=1, keepdim=True).clamp(min=1e-12)
+    a = torch.sigmoid(y[:, 3:6])
+    r = 0.09 + 0.91 * torch.sigmoid(y[:, 6])
+    return a, r, n
+
+
+def positional_encoding(w: torch.Tensor) -> torch.Tensor:
+    """PE(w) = [w, sin(pi w), cos(pi w), sin(2 pi w), cos(2 pi w), ..., k = 0..3]."""
+    parts = [w]
+    for k in range(N_FREQ):
+        arg = (2.0 ** k) * math.pi * w
+        parts.append(torch.sin(arg))
+        parts.append(torch.cos(arg))
+    return torch.cat(parts, dim=-1)
+
+
+def depth_from_logit(t_hat: torch.Tensor, near: float, far: float) -> torch.Tensor:
+    """t = near + (far - near) * min(t_hat, 1): normalised depth clamped to far."""
+    return near + (far - near) * torch.clamp(t_hat, max=1.0)
+
+
+def implicit_ray_tracer(f: torch.Tensor, w: torch.Tensor, layers: Layers,
+                        near: float, far: float):
+    """v, t = I(f, w): soft visibility in (0, 1) and expected depth in [near, far]."""
+    y = mlp3(torch.cat([f, positional_encoding(w)], dim=-1), layers)
+    v = torch.sigmoid(y[:, 0])
+    t = depth_from_logit(torch.nn.functional.softplus(y[:, 1]), near, far)
+    return v, t

@@ -1,0 +1,211 @@
+"""The whole hash-renderer path and its FP64 gradient  (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+For every primary point x with normal n, view direction w_o, albedo a and
+roughness r (the G-buffer that the paper's CNN renderer G would produce;
+Sec. 3.2 overview), following the paper's order (Sec. 3.1, Sec. 3.2
+overview):
+
+  (a) f = H(x)
+      for each of N directions w_i (cosine-weighted about n):
+  (c)     v_i, t_i = I(f, w_i)
+  (d)     x'_i = x + t_i w_i;  f'_i = H(x'_i)
+  (b)     a'_i, r'_i, n'_i = B(f'_i)
+          for each of M directions w'_ij (cosine-weighted about n'_i):
+  (c)         v'_ij = I(f'_i, w'_ij)
+  (e)     L'_o,i = (pi/M) sum_j v'_ij L_env(w'_ij) f_r(a'_i, r'_i, n'_i; w'_ij, -w_i)
+          L(x, w_i) = v_i L_env(w_i) + (1 - v_i) L'_o,i                 (Eq. 2)
+  (e) L(x, w_o) = (pi/N) sum_i L(x, w_i) f_r(a, r, n; w_i, w_o)          (Eq. 1)
+
+Readings (the paper's inference uses hard visibility and only bounces
+shadow rays, Sec. 3.2): the default is the soft, differentiable form of
+Eq. 2 in which every direction bounces with weight (1 - v);  `force_vis`
+and `force_vis2` pin v or v' to a constant (used by the furnace tests);
+`lambert` drops the specular lobe.  There is no third bounce: the secondary
+sum keeps only the environment light that reaches x' (v'), as in the
+paper's "collect only visible rays".
+
+Gradient (distillation pattern): the loss is 1/2 mean over pixels and
+channels of (L_student - L_teacher)^2; torch autograd in float64 supplies
+its exact derivative with respect to the hash table and all MLP weights.
+Sampled directions are constants of the estimator: w'_ij is drawn about
+the detached n'_i.  Pins: central finite differences of this forward
+(tests/test_oracle_render.py).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, Optional
+
+import numpy as np
+import torch
+
+from . import hashgrid, mlp, sampling, shading
+
+
+@dataclasses.dataclass(frozen=True)
+class Options:
+    n_dirs: int
+    m_dirs: int = 8
+    levels: int = 16
+    log2_T: int = 19
+    base_res: int = 16
+    max_res: int = 2048
+    near: float = 0.05
+    far: float = 1.5
+    f0: float = shading.F0_DEFAULT
+    lambert: bool = False
+    force_vis: float = -1.0      # < 0: use I's visibility
+    force_vis2: float = -1.0
+    dir_seed: int = 0x5EED
+    dense_coarse: bool = True
+
+    @staticmethod
+    def from_config(cfg, **kw) -> "Options":
+        return Options(n_dirs=cfg.n_dirs, m_dirs=cfg.m_dirs, levels=cfg.levels,
+                       log2_T=cfg.log2_T, base_res=cfg.base_res, max_res=cfg.max_res,
+                       near=cfg.near, far=cfg.far, f0=cfg.f0, dir_seed=cfg.dir_seed, **kw)
+
+
+@dataclasses.dataclass
+class Params:
+    """Float64 model parameters (may require grad)."""
+    table: torch.Tensor                 # [L, T, F]
+    brdf: list                          # [(W, b)] x 3
+    irt: list
+    env: torch.Tensor                   # [H, W, 4]
+
+    @staticmethod
+    def from_arrays(table, brdf_layers, irt_layers, env, requires_grad=False) -> "Params":
+        t = torch.tensor(np.asarray(table, np.float64), requires_grad=requires_grad)
+        b = [(torch.tensor(np.asarray(w, np.float64), requires_grad=requires_grad),
+              torch.tensor(np.asarray(c, np.float64), requires_grad=requires_grad))
+             for w, c in brdf_layers]
+        i = [(torch.tensor(np.asarray(w, np.float64), requires_grad=requires_grad),
+              torch.tensor(np.asarray(c, np.float64), requires_grad=requires_grad))
+             for w, c in irt_layers]
+        return Params(t, b, i, torch.tensor(np.asarray(env, np.float64)))
+
+
+def _gbuffer_tensors(gb: Dict[str, np.ndarray], rows: np.ndarray):
+    def g(key, k):
+        return torch.from_numpy(np.asarray(gb[key][rows, :k], np.float64))
+    ar = torch.from_numpy(np.asarray(gb["albedo_rough"][rows], np.float64))
+    return g("pos", 3), g("normal", 3), g("view", 3), ar[:, :3], ar[:, 3]
+
+
+def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, opt: Options,
+                  fixed_dirs: Optional[torch.Tensor] = None, want_dirs: bool = False):
+    """Radiance [P, 3] of P primary points with global pixel ids (RNG keys)."""
+    P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
+    res = hashgrid.level_resolutions(opt.levels, opt.base_res, opt.max_res)
+    dense = hashgrid.dense_levels(res, 1 << opt.log2_T, opt.dense_coarse)
+
+    # (a) primary feature
+    f = hashgrid.encode(x, prm.table, res, dense)
+
+    # primary directions, slot 0 of sample q = gid * N + i
+    q = np.asarray(global_ids, np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
+    w_i = sampling.cosine_direction(n[:, None, :], u1, u2)                 # [P, N, 3]
+
+    # (c) visibility and depth along w_i
+    f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
+    v, t = mlp.implicit_ray_tracer(f_rep, w_i.reshape(P * N, 3), prm.irt, opt.near, opt.far)
+    if opt.force_vis >= 0:
+        v = torch.full_like(v, opt.force_vis)
+
+    # (d) bounce and re-encode
+    x2 = x[:, None, :] + t.reshape(P, N, 1) * w_i                          # x' = x + t w
+    f2 = hashgrid.encode(x2.reshape(P * N, 3), prm.table, res, dense)
+    a2, r2, n2 = mlp.brdf_decoder(f2, prm.brdf)                           # (b)
+
+    # secondary directions, slots 1..M about the (detached) secondary normal
+    if fixed_dirs is None:
+        slots = 1 + np.arange(M, dtype=np.uint64)
+        u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q.reshape(-1, 1), slots[None, :], M))
+        w_j = sampling.cosine_direction(n2.detach()[:, None, :], u1, u2)   # [P*N, M, 3]
+    else:
+        w_j = fixed_dirs
+    f2_rep = f2[:, None, :].expand(P * N, M, f2.shape[1]).reshape(P * N * M, -1)
+    v2, _ = mlp.implicit_ray_tracer(f2_rep, w_j.reshape(-1, 3), prm.irt, opt.near, opt.far)
+    v2 = v2.reshape(P * N, M)
+    if opt.force_vis2 >= 0:
+        v2 = torch.full_like(v2, opt.force_vis2)
+
+    # (e) secondary sum at x' towards -w_i (Eq. 1 at x')
+    wo2 = -w_i.reshape(P * N, 1, 3)
+    fr2 = shading.brdf(a2[:, None, :], r2[:, None], n2[:, None, :], w_j, wo2, opt.f0, opt.lambert)
+    le2 = shading.env_lookup(prm.env, w_j)
+    lo2 = shading.mc_sum(v2[..., None] * le2 * fr2, M).reshape(P, N, 3)
+
+    # Eq. 2, then Eq. 1 at x
+    v = v.reshape(P, N, 1)
+    li = v * shading.env_lookup(prm.env, w_i) + (1.0 - v) * lo2
+    fr1 = shading.brdf(albedo[:, None, :], rough[:, None], n[:, None, :], w_i, wo[:, None, :],
+                       opt.f0, opt.lambert)
+    out = shading.mc_sum(li * fr1, N)
+    if want_dirs:
+        return out, w_j.detach()
+    return out
+
+
+def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
+           rows: Optional[np.ndarray] = None, chunk_rows: int = 1 << 17) -> np.ndarray:
+    """Radiance [len(rows), 3] (float64) of G-buffer rows (default: all).
+
+    The RNG key of row p is pixel_offset + p, so a frame rendered in pieces
+    equals the frame rendered at once.
+    """
+    P = gb["pos"].shape[0]
+    rows = np.arange(P) if rows is None else np.asarray(rows)
+    per = max(1, chunk_rows // (opt.n_dirs * opt.m_dirs))
+    out = []
+    with torch.no_grad():
+        for s in range(0, rows.size, per):
+            r = rows[s:s + per]
+            out.append(render_points(*_gbuffer_tensors(gb, r), pixel_offset + r, prm, opt).numpy())
+    return np.concatenate(out, axis=0) if out else np.zeros((0, 3))
+
+
+def distill_loss(gb, rows, student: Params, target: torch.Tensor, opt: Options,
+                 pixel_offset: int = 0, fixed_dirs=None, want_dirs=False):
+    """1/2 mean over rays and channels of (L_student - L_teacher)^2."""
+    r = np.asarray(rows)
+    out = render_points(*_gbuffer_tensors(gb, r), pixel_offset + r, student, opt,
+                        fixed_dirs=fixed_dirs, want_dirs=want_dirs)
+    if want_dirs:
+        out, dirs = out
+    loss = 0.5 * ((out - target) ** 2).mean()
+    return (loss, dirs) if want_dirs else loss
+
+
+def distill_gradient(gb, rows, student: Params, target: torch.Tensor, opt: Options,
+                     pixel_offset: int = 0):
+    """FP64 loss and its gradient w.r.t. the table and both MLPs' packed weights."""
+    for p in _leaves(student):
+        p.grad = None
+    loss = distill_loss(gb, rows, student, target, opt, pixel_offset)
+    loss.backward()
+    g_table = student.table.grad.clone()
+    g_brdf = torch.cat([t.grad.reshape(-1) for wb in student.brdf for t in wb])
+    g_irt = torch.cat([t.grad.reshape(-1) for wb in student.irt for t in wb])
+    return float(loss), g_table, g_brdf, g_irt
+
+
+def upstream_gradient(student_rad: np.ndarray, target_rad: np.ndarray) -> np.ndarray:
+    """dLoss/dL_student for the distillation loss: (L_s - L_t) / (3 P) per channel."""
+    return (student_rad - target_rad) / (3.0 * student_rad.shape[0])
+
+
+def _leaves(p: Params):
+    yield p.table
+    for w, b in p.brdf + p.irt:
+        yield w
+        yield b
+
+
+def secondary_samples_per_second(opt: Options, n_pixels: int, seconds: float) -> float:
+    return n_pixels * opt.n_dirs / seconds
+
