@@ -1,0 +1,299 @@
+"""Benchmark: secondary samples/s and ms per 800x800 frame of the fused renderer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16] [--impl ours|reference]
+
+One step renders one 800x800 frame (N = 128 directions per pixel, M = 8 per
+secondary point, L = 16 levels, T = 2^19, resolutions 16..2048, 64x128 env)
+through the C ABI, i.e. one launch of the fused kernel.  Four seeded scenes
+(tables, MLPs, env maps and G-buffers, about 420 MB in FP32) are rotated
+step by step, so every step starts with its inputs out of the 129 MB L2.
+Under torchrun each rank renders its own scenes (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the only other place this script runs oracle/).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenegen  # noqa: E402
+
+METRIC = "secondary samples/s & ms/frame at 800² (BF16 vs FP32, ≥45 dB PSNR vs FP64)"
+UNIT = "samples/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 FFMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_NOTE = "4 scenes rotated, one per step (~105 MB each in FP32, 420 MB total > 129 MB L2)"
+
+
+def algorithmic_flop_per_sample(cfg) -> int:
+    """MLP multiply-adds x 2 per secondary sample, unpadded: (1 + M) I evaluations and one B."""
+    lf = cfg.levels * 2
+    irt = (lf + 27) * 64 + 64 * 64 + 64 * 2
+    brdf = lf * 64 + 64 * 64 + 64 * 7
+    return 2 * ((1 + cfg.m_dirs) * irt + brdf)
+
+
+def workload_name(cfg) -> str:
+    return (f"{cfg.name}: {cfg.width}x{cfg.height} px, N={cfg.n_dirs}, M={cfg.m_dirs}, L={cfg.levels}, "
+            f"T=2^{cfg.log2_T}, res {cfg.base_res}-{cfg.max_res}, env {cfg.env_h}x{cfg.env_w}, {cfg.precision}")
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(cfg, seconds: float, seed: int = 0):
+    """Samples/s of the FP64 oracle on a bounded pixel sample of the workload (host cores)."""
+    import torch
+    from oracle import render as orender
+    sc = scenegen.make_scene(cfg, seed)
+    gb = scenegen.make_gbuffer(cfg.n_pixels, seed)
+    prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, sc.env)
+    opt = orender.Options.from_config(cfg)
+    rows = scenegen.subset_permutation(cfg.n_pixels, cfg.n_pixels, seed=1)
+    chunk = max(1, (1 << 15) // cfg.n_dirs)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        orender.render(gb, prm, opt, rows=rows[done:done + chunk])
+        done += chunk
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= cfg.n_pixels:
+            break
+    return done * cfg.n_dirs / el, done, el, torch.get_num_threads()
+
+
+def run_reference(args, cfg):
+    rank, _, world = dist_info()
+    if rank != 0:
+        return
+    rate_steps = []
+    per_step = max(1.0, args.ref_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(cfg, 0.2)
+    samples, secs = 0, 0.0
+    for _ in range(args.steps):
+        r, done, el, cores = cpu_oracle_rate(cfg, per_step)
+        samples += done * cfg.n_dirs
+        secs += el
+        rate_steps.append(r)
+    value = samples / secs
+    ms_frame = cfg.samples / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "ms_per_frame": ms_frame, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{samples // cfg.n_dirs} pixels of the 800x800 frame over {args.steps} steps "
+                                       f"(~{per_step:.0f} s each), extrapolated to samples/s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+    rank, local, world = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2409_10327_gb300 import binding
+
+    n_scenes = 4
+    renderers, gbs = [], []
+    for s in range(n_scenes):
+        seed = rank * n_scenes + s
+        sc = scenegen.make_scene(cfg, seed)
+        r = binding.Renderer(binding.make_config(cfg))
+        table = torch.from_numpy(sc.table).cuda()
+        if cfg.precision == "bf16":
+            table = table.half()
+        r.set_params(table, torch.from_numpy(sc.brdf_blob).cuda(), torch.from_numpy(sc.irt_blob).cuda(),
+                     torch.from_numpy(sc.env).cuda())
+        renderers.append(r)
+        gbs.append({k: torch.from_numpy(v).cuda() for k, v in scenegen.make_gbuffer(cfg.n_pixels, seed).items()})
+    out = torch.empty(cfg.n_pixels, 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(args.warmup):
+        renderers[w % n_scenes].render_frame(gbs[w % n_scenes], out=out)
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        renderers[k % n_scenes].render_frame(gbs[k % n_scenes], out=out)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * cfg.samples * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host G-buffer -> device, render, radiance -> host
+    host_gb = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in gbs]
+    host_out = torch.empty(cfg.n_pixels, 4).pin_memory()
+    staging = {k: torch.empty_like(v) for k, v in gbs[0].items()}
+    for w in range(max(1, args.warmup)):
+        renderers[w % n_scenes].render_frame_host(host_gb[w % n_scenes], host_out, staging, out)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        renderers[k % n_scenes].render_frame_host(host_gb[k % n_scenes], host_out, staging, out)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = sum(v.numel() * v.element_size() for v in host_gb[0].values())
+    d2h = host_out.numel() * host_out.element_size()
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    flop = algorithmic_flop_per_sample(cfg) * cfg.samples
+    avg_launch_s = sum(launch_ms) / len(launch_ms) / 1e3
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    if cfg.precision == "fp32":
+        roof = {"bound": "alu", "achieved": flop / avg_launch_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal)"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "achieved": flop / avg_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s",
+                "peak_source": "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["algorithmic_per_launch"] = flop
+    roof["kernel_ms"] = avg_launch_s * 1e3
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, done, el, cores = cpu_oracle_rate(cfg, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{done} pixels ({done * cfg.n_dirs} secondary samples) of one 800x800 frame, {el:.1f} s"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if cfg.precision == "fp32" else "bf16",
+            "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": n_scenes},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": args.steps, "clocks": clk,
+            "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms)}}
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="frame800")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    import dataclasses
+    cfg = dataclasses.replace(scenegen.CONFIGS[args.config], precision=args.precision)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

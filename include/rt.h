@@ -1,0 +1,210 @@
+/*
+ * rt.h -- C ABI of the GB300 hash-grid secondary-ray renderer.
+ *
+ * The renderer is the "hash grid-based renderer" of Baking Relightable NeRF
+ * for Real-time Direct/Indirect Illumination Rendering (arXiv 2409.10327):
+ * for every primary surface point x (a G-buffer texel produced upstream)
+ *
+ *   (a) f = H(x)                       multi-resolution hash encoding  (Sec. 3.2)
+ *   (c) v_i, t_i = I(f, w_i)           implicit ray tracer MLP          (Sec. 3.2)
+ *   (d) x'_i = x + t_i w_i, f'_i = H(x'_i)                              (Sec. 3.1)
+ *   (b) a'_i, r'_i, n'_i = B(f'_i)     BRDF decoder MLP                 (Sec. 3.2, 3.3)
+ *   (c) v'_ij = I(f'_i, w'_ij)         M directions per secondary point (suppl. "Rendering Details")
+ *   (e) L'_o,i = (pi/M) sum_j v'_ij Lenv(w'_ij) f_r(a'_i, r'_i, n'_i; w'_ij, -w_i)    (Eq. 1 at x')
+ *       L(x, w_i) = v_i Lenv(w_i) + (1 - v_i) L'_o,i                                (Eq. 2)
+ *       L(x, w_o) = (pi/N) sum_i L(x, w_i) f_r(a, r, n; w_i, w_o)                   (Eq. 1)
+ *
+ * with cosine-weighted directions (so (w.n)/p(w) = pi), soft visibility,
+ * the simplified Disney BRDF (GGX D with alpha = r^2, Schlick F with F0,
+ * height-correlated Smith visibility; Sec. 4.1, Sec. 4.2, Sec. 5) and an
+ * equirectangular environment map with bilinear texel interpolation (Sec. 2.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller, unless a
+ *    comment says "host".  The library keeps the table and env pointers given
+ *    to rt_set_params by reference: they must stay valid and unchanged while
+ *    calls that read them are in flight.
+ *  - float4 planes ([P][4] floats) must be 16-byte aligned; other arrays
+ *    4-byte aligned.  Misaligned or NULL required pointers return
+ *    RT_ERR_INVALID_ARG before anything is launched.
+ *  - Every compute call is asynchronous on the caller's stream (`stream` is a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream), performs
+ *    no allocation and no host synchronisation.  Launch failures return
+ *    RT_ERR_CUDA; asynchronous device faults surface from a later CUDA call.
+ *  - P = 0 is valid and launches nothing.  P is limited to 2^31 - 1.
+ *  - Random directions come from SplitMix64 (Steele, Lea & Flood 2014):
+ *    output k >= 1 of the generator started at state = dir_seed.  Slot c of
+ *    secondary sample q (q = pixel * N + i) has counter q*(M+1) + c; slot 0 is
+ *    the primary direction w_i, slot 1 + j the j-th direction at x'_i;
+ *    counter k draws outputs 2k+1 and 2k+2 for (u1, u2) = top 24 bits * 2^-24.
+ *    The direction is normalize(n + s), s = (2 sqrt(u1(1-u1)) cos 2pi u2,
+ *    2 sqrt(u1(1-u1)) sin 2pi u2, 1 - 2 u1) uniform on the sphere.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rt_status {
+  RT_OK = 0,
+  RT_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or config field */
+  RT_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  RT_ERR_OOM = 3,           /* rt_create could not allocate its workspace */
+  RT_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
+  RT_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (status word) */
+  RT_ERR_BOUNDS = 6,        /* a device-side bounds check fired (status word) */
+  RT_ERR_NOT_READY = 7      /* rt_set_params has not been called */
+} rt_status;
+
+enum { RT_FP32 = 0, RT_BF16 = 1 };        /* precision                          */
+enum { RT_DISNEY = 0, RT_LAMBERT = 1 };   /* brdf_mode                          */
+
+/* Sizes and constants of one renderer instance.  Defaults: rt_config_default. */
+typedef struct rt_config {
+  int32_t levels;        /* L, 1..16 hash levels (paper: 14)                     */
+  int32_t feat_dim;      /* F, features per entry; must be 2 (paper: 2)          */
+  int32_t log2_T;        /* T = 2^log2_T entries per level, 8..24 (paper: 17)    */
+  int32_t base_res;      /* N_min >= 2                                          */
+  int32_t max_res;       /* N_max >= N_min, <= 2^20                             */
+  int32_t dense_coarse;  /* 1: levels with (N_l+1)^3 <= T are indexed densely   */
+  int32_t precision;     /* RT_FP32: float table, FP32 MLPs.
+                            RT_BF16: half table, BF16 MLP operands, FP32 accum  */
+  int32_t n_dirs;        /* N, directions per primary point, 1..4096           */
+  int32_t m_dirs;        /* M, directions per secondary point, 1..64 (paper: 8) */
+  int32_t brdf_mode;     /* RT_DISNEY or RT_LAMBERT (diffuse lobe only)         */
+  float near_t, far_t;   /* depth range of I (paper: 0.05, 1.5)                 */
+  float f0;              /* Schlick F0 (paper: 0.04)                            */
+  float force_vis;       /* < 0: v from I; else v := force_vis  (0..1)          */
+  float force_vis2;      /* < 0: v' from I; else v' := force_vis2 (0..1)        */
+  int32_t env_h, env_w;  /* environment map size, each 1..8192                  */
+  uint64_t dir_seed;     /* SplitMix64 starting state of the direction sampler  */
+} rt_config;
+
+/* Four [P][4] float planes describing primary surface points (device). */
+typedef struct rt_gbuffer {
+  const float* pos;           /* x.xyz, .w ignored                               */
+  const float* normal;        /* unit n.xyz                                      */
+  const float* view;          /* unit w_o.xyz, pointing away from the surface     */
+  const float* albedo_rough;  /* albedo rgb in .xyz, roughness in .w              */
+} rt_gbuffer;
+
+typedef struct rt_ctx rt_ctx;
+
+/* ---- host-only helpers (no GPU needed) --------------------------------- */
+
+/* Status name, e.g. "RT_ERR_INVALID_ARG".  Never NULL. */
+const char* rt_status_str(rt_status s);
+
+/* Fill *cfg with the 800x800 workload's defaults (L=16, T=2^19, 16..2048,
+ * N=128, M=8, FP32, Disney, near 0.05, far 1.5, F0 0.04, env 64x128). */
+rt_status rt_config_default(rt_config* cfg);
+
+/* RT_OK if every field is in range, else RT_ERR_INVALID_ARG. */
+rt_status rt_config_validate(const rt_config* cfg);
+
+/* Level resolution N_l = floor(N_min b^l), b = exp((ln N_max - ln N_min)/(L-1))
+ * (Instant-NGP's ladder, referenced in Sec. 3.2), computed in double with a
+ * 1e-9 guard; -1 for an invalid config or level. */
+int32_t rt_level_resolution(const rt_config* cfg, int32_t level);
+
+/* 1 if level l is indexed densely, 0 if hashed, -1 if invalid. */
+int32_t rt_level_is_dense(const rt_config* cfg, int32_t level);
+
+/* Float counts of the parameter blobs: which = 0 table (L*T*F entries),
+ * 1 BRDF decoder B, 2 implicit ray tracer I; -1 if invalid.
+ * MLP blob layout (both): W1 [64][in], b1 [64], W2 [64][64], b2 [64],
+ * W3 [out][64], b3 [out]; row-major, weights as (out, in).  B: in = L*F,
+ * out = 7 ([n(3), a(3), r]).  I: in = L*F + 27 ([f, PE(w)] with
+ * PE(w) = [w, sin(2^k pi w), cos(2^k pi w)] for k = 0..3), out = 2. */
+int64_t rt_param_count(const rt_config* cfg, int32_t which);
+
+/* Bytes of device memory that rt_create allocates for this config. */
+int64_t rt_workspace_bytes(const rt_config* cfg);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Validate cfg and allocate the context's workspace on the current device
+ * (packed weights, status word).  *out stays NULL on failure. */
+rt_status rt_create(const rt_config* cfg, rt_ctx** out);
+
+/* Free the workspace; synchronises the device first.  NULL is a no-op. */
+rt_status rt_destroy(rt_ctx* ctx);
+
+/* Bind the model: table [L][T][F] (float for RT_FP32, IEEE half for RT_BF16;
+ * kept by reference), B and I blobs (float, layout of rt_param_count; copied
+ * and repacked on `stream` into the context) and env [env_h][env_w][4] float
+ * (rgb + ignored lane; kept by reference).  Call again after the weights
+ * change. */
+rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, const float* irt_w,
+                        const float* env, void* stream);
+
+/* Read (and clear) the device status word written by bounded waits and
+ * bounds checks; synchronises `stream`.  *word = 0 when nothing fired. */
+rt_status rt_check(rt_ctx* ctx, uint32_t* word, void* stream);
+
+/* ---- stages ------------------------------------------------------------- */
+
+/* Stage (a), f = H(x) (Sec. 3.2).  pos [P][4]; feat [P][L*F] (float, level-
+ * major, F inner).  Optional idx [P][L][8] (uint32 table row within the
+ * level) and w [P][L][8] (trilinear weight), corner c at offset
+ * (c&1, c>>1&1, c>>2&1).  The grid coordinate is u = x*0.5 + 0.5 clamped to
+ * [0,1], g = u * N_l, each rounded to float32 (no contraction), cell
+ * i0 = min(floor(g), N_l - 1), w = g - i0: indices are bit-exact
+ * reproducible.  Dense rows: i + j(N+1) + k(N+1)^2; hashed rows:
+ * (i ^ j*2654435761 ^ k*805459861) mod T in uint32 arithmetic. */
+rt_status rt_encode(rt_ctx* ctx, const float* pos, int64_t P, float* feat, uint32_t* idx, float* w,
+                    void* stream);
+
+/* Stage (b), a, r, n = B(f) (Sec. 3.2, Sec. 3.3).  feat [P][L*F] float;
+ * brdf [P][8] = (n.xyz normalised, a.rgb = sigmoid, r = 0.09 + 0.91 sigmoid, 0). */
+rt_status rt_decode(rt_ctx* ctx, const float* feat, int64_t P, float* brdf, void* stream);
+
+/* Stage (c), v, t = I(f, w) (Sec. 3.2).  feat [P][L*F]; dirs [P][K][4] unit
+ * directions; vis [P][K] = sigmoid(z0); depth [P][K] = near + (far - near) *
+ * min(softplus(z1), 1).  K in 1..4096. */
+rt_status rt_trace(rt_ctx* ctx, const float* feat, const float* dirs, int64_t P, int32_t K,
+                   float* vis, float* depth, void* stream);
+
+/* Direction sampler (header conventions).  level 0: K = N directions about
+ * normal[p] for primary point p, sample ids (index_offset + p)*N + i, slot 0.
+ * level 1: K = M directions about normal[q] for secondary sample
+ * q' = index_offset + q, slots 1..M.  normal [P][4]; dirs [P][K][4]. */
+rt_status rt_sample(rt_ctx* ctx, const float* normal, int64_t P, int32_t level, int64_t index_offset,
+                    float* dirs, void* stream);
+
+/* Stage (e) at one level, directions regenerated as in rt_sample.
+ * level 0 (Eq. 1 + Eq. 2): out[p] = (pi/N) sum_i (vis[p][i] Lenv(w_i) +
+ *   (1 - vis[p][i]) lin[p][i]) f_r(pts[p]; w_i, view[p]); lin [P][N][4] may be
+ *   NULL (treated as 0).
+ * level 1 (Eq. 1 at x'): out[q] = (pi/M) sum_j vis[q][j] Lenv(w'_j) f_r(pts[q]; w'_j, view[q]);
+ *   lin must be NULL.  view[q] is -w_i for a secondary point.
+ * out [P][4] float (rgb, 0).  force_vis / force_vis2 are NOT applied here. */
+rt_status rt_shade(rt_ctx* ctx, const rt_gbuffer* pts, int64_t P, int32_t level, int64_t index_offset,
+                   const float* vis, const float* lin, float* out, void* stream);
+
+/* ---- the fused hot path -------------------------------------------------- */
+
+/* Stages (a)-(e) fused in one persistent kernel: radiance [P][4] (rgb, 0) of
+ * the P G-buffer points; point p uses RNG pixel id pixel_offset + p, so a
+ * frame rendered in shards equals the frame rendered at once. */
+rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
+                          float* radiance, void* stream);
+
+/* Adjoint of rt_render_frame for an upstream gradient d_radiance [P][4]
+ * (lane 3 ignored): ACCUMULATES dLoss/dtable into g_table [L][T][F] float and
+ * dLoss/dweights into g_brdf / g_irt (float, blob layouts).  Sampled
+ * directions are constants of the estimator.  The caller zeroes the
+ * gradient buffers. */
+rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
+                      const float* d_radiance, float* g_table, float* g_brdf, float* g_irt,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

@@ -60,6 +60,12 @@ class Options:
     force_vis2: float = -1.0
     dir_seed: int = 0x5EED
     dense_coarse: bool = True
+    # conditioning probe: relative Gaussian jitter of the secondary points x'
+    # (0 = off), keyed by (jitter_seed, pixel id); used only to measure how
+    # strongly the exact result reacts to float32-sized rounding of x'.
+    x2_jitter: float = 0.0
+    s_jitter: float = 0.0        # absolute jitter of the sphere points s of both samplers
+    jitter_seed: int = 0
 
     @staticmethod
     def from_config(cfg, **kw) -> "Options":
@@ -108,7 +114,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     # primary directions, slot 0 of sample q = gid * N + i
     q = np.asarray(global_ids, np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
     u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
-    w_i = sampling.cosine_direction(n[:, None, :], u1, u2)                 # [P, N, 3]
+    w_i = sampling.cosine_direction(n[:, None, :], u1, u2, _jitter(opt, global_ids, 0, (N, 3)))   # [P, N, 3]
 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
@@ -118,6 +124,8 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # (d) bounce and re-encode
     x2 = x[:, None, :] + t.reshape(P, N, 1) * w_i                          # x' = x + t w
+    if opt.x2_jitter > 0:
+        x2 = x2 * (1.0 + opt.x2_jitter * _noise(opt, global_ids, 2, (N, 3)))
     f2 = hashgrid.encode(x2.reshape(P * N, 3), prm.table, res, dense)
     a2, r2, n2 = mlp.brdf_decoder(f2, prm.brdf)                           # (b)
 
@@ -125,7 +133,8 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     if fixed_dirs is None:
         slots = 1 + np.arange(M, dtype=np.uint64)
         u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q.reshape(-1, 1), slots[None, :], M))
-        w_j = sampling.cosine_direction(n2.detach()[:, None, :], u1, u2)   # [P*N, M, 3]
+        w_j = sampling.cosine_direction(n2.detach()[:, None, :], u1, u2,
+                                        _jitter(opt, global_ids, 1, (N, M, 3), flat=True))   # [P*N, M, 3]
     else:
         w_j = fixed_dirs
     f2_rep = f2[:, None, :].expand(P * N, M, f2.shape[1]).reshape(P * N * M, -1)
@@ -151,6 +160,18 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     return out
 
 
+def _noise(opt: Options, global_ids, stream: int, shape) -> torch.Tensor:
+    return torch.from_numpy(np.stack([np.random.default_rng([opt.jitter_seed, stream, int(g)]).standard_normal(shape)
+                                      for g in np.asarray(global_ids)]))
+
+
+def _jitter(opt: Options, global_ids, stream: int, shape, flat: bool = False):
+    if opt.s_jitter <= 0:
+        return None
+    z = opt.s_jitter * _noise(opt, global_ids, stream, shape)
+    return z.reshape(-1, *shape[1:]) if flat else z
+
+
 def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
            rows: Optional[np.ndarray] = None, chunk_rows: int = 1 << 17) -> np.ndarray:
     """Radiance [len(rows), 3] (float64) of G-buffer rows (default: all).
@@ -167,6 +188,28 @@ def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: i
             r = rows[s:s + per]
             out.append(render_points(*_gbuffer_tensors(gb, r), pixel_offset + r, prm, opt).numpy())
     return np.concatenate(out, axis=0) if out else np.zeros((0, 3))
+
+
+def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
+                        rows: Optional[np.ndarray] = None, rel: float = 2.0 ** -23, draws: int = 2) -> np.ndarray:
+    """Per-pixel, per-channel max |L(jittered) - L| over `draws` float32-sized jitters.
+
+    Two inputs of the exact result are ill-conditioned at float32 scale:
+    the secondary points x' = x + t w feed the finest hash levels, whose
+    features change by up to ~N_l * |table step| per unit of x'; and a
+    grazing direction normalize(n + s) moves by |ds| / |n + s| when n + s is
+    short.  A pixel dominated by such a sample under a sharp specular lobe
+    can move by far more than 1e-4 when x' or s changes by one float32
+    rounding.  This probe jitters x' (relative) and s (absolute) by `rel`
+    and reports how far the exact result moves; the FP32 parity tests scale
+    their per-pixel bound by it.
+    """
+    base = render(gb, prm, opt, pixel_offset, rows)
+    worst = np.zeros_like(base)
+    for d in range(draws):
+        o = dataclasses.replace(opt, x2_jitter=rel, s_jitter=rel, jitter_seed=1 + d)
+        worst = np.maximum(worst, np.abs(render(gb, prm, o, pixel_offset, rows) - base))
+    return worst
 
 
 def distill_loss(gb, rows, student: Params, target: torch.Tensor, opt: Options,

@@ -77,12 +77,17 @@ def uniform_sphere(u1: torch.Tensor, u2: torch.Tensor) -> torch.Tensor:
     return torch.stack([rho * torch.cos(phi), rho * torch.sin(phi), z], dim=-1)
 
 
-def cosine_direction(n: torch.Tensor, u1: torch.Tensor, u2: torch.Tensor) -> torch.Tensor:
+def cosine_direction(n: torch.Tensor, u1: torch.Tensor, u2: torch.Tensor, s_jitter=None) -> torch.Tensor:
     """Cosine-weighted direction about the unit normal n: normalize(n + s).
 
-    The degenerate draw s = -n (probability zero) returns n.
+    The degenerate draw s = -n (probability zero) returns n.  `s_jitter`
+    (optional, same shape as s) is added to s by the conditioning probe of
+    ``render.float32_sensitivity`` only.
     """
-    d = n + uniform_sphere(u1, u2)
+    s = uniform_sphere(u1, u2)
+    if s_jitter is not None:
+        s = s + s_jitter
+    d = n + s
     l2 = (d * d).sum(-1, keepdim=True)
     safe = torch.where(l2 > 1e-20, l2, torch.ones_like(l2))
     return torch.where(l2 > 1e-20, d / torch.sqrt(safe), n.expand_as(d))

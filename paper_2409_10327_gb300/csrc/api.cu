@@ -1,0 +1,328 @@
+// Host side of the C ABI declared in include/rt.h: validation, the context,
+// and the launches.  No entry point allocates except rt_create.
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+
+#include "rt_internal.h"
+
+using namespace rtk;
+
+struct rt_ctx {
+  rt_config cfg;
+  int device;
+  int num_sms;
+  int res[kMaxLevels];
+  int dense[kMaxLevels];
+  float* wpack;        // WPACK_FLOATS
+  uint32_t* status;    // device status word
+  const void* table;
+  const float* env;
+  bool ready;
+};
+
+namespace {
+
+constexpr int64_t kMaxP = 2147483647LL;
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int level_res(const rt_config* c, int l) {
+  if (c->levels == 1) return c->base_res;
+  const double b = std::exp((std::log((double)c->max_res) - std::log((double)c->base_res)) / (c->levels - 1));
+  return (int)std::floor((double)c->base_res * std::pow(b, (double)l) + 1e-9);
+}
+
+bool level_dense(const rt_config* c, int res) {
+  if (!c->dense_coarse) return false;
+  const double n1 = (double)res + 1.0;
+  return n1 * n1 * n1 <= (double)(1LL << c->log2_T);
+}
+
+ModelDesc model_desc(const rt_ctx* ctx) {
+  ModelDesc m{};
+  const rt_config& c = ctx->cfg;
+  m.grid.levels = c.levels;
+  m.grid.log2T = c.log2_T;
+  m.grid.mask = (uint32_t)((1ULL << c.log2_T) - 1ULL);
+  m.grid.half = c.precision == RT_BF16 ? 1 : 0;
+  m.grid.table = ctx->table;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    m.grid.res[l] = l < c.levels ? ctx->res[l] : 1;
+    m.grid.dense[l] = l < c.levels ? ctx->dense[l] : 0;
+  }
+  m.wpack = ctx->wpack;
+  m.env = reinterpret_cast<const float4*>(ctx->env);
+  m.env_h = c.env_h;
+  m.env_w = c.env_w;
+  m.lf = c.levels * c.feat_dim;
+  m.lfp = (m.lf + 7) / 8 * 8;
+  m.N = c.n_dirs;
+  m.M = c.m_dirs;
+  m.near_t = c.near_t;
+  m.far_t = c.far_t;
+  m.f0 = c.f0;
+  m.force_vis = c.force_vis;
+  m.force_vis2 = c.force_vis2;
+  m.lambert = c.brdf_mode == RT_LAMBERT;
+  m.seed = c.dir_seed;
+  return m;
+}
+
+rt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RT_OK : RT_ERR_CUDA; }
+
+rt_status check_ctx(const rt_ctx* ctx) {
+  if (ctx == nullptr) return RT_ERR_INVALID_ARG;
+  if (!ctx->ready) return RT_ERR_NOT_READY;
+  return RT_OK;
+}
+
+bool check_plane(const float* p) { return p != nullptr && aligned(p, 16); }
+
+bool check_gbuffer(const rt_gbuffer* gb) {
+  return gb != nullptr && check_plane(gb->pos) && check_plane(gb->normal) && check_plane(gb->view) &&
+         check_plane(gb->albedo_rough);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rt_status_str(rt_status s) {
+  switch (s) {
+    case RT_OK: return "RT_OK";
+    case RT_ERR_INVALID_ARG: return "RT_ERR_INVALID_ARG";
+    case RT_ERR_UNSUPPORTED: return "RT_ERR_UNSUPPORTED";
+    case RT_ERR_OOM: return "RT_ERR_OOM";
+    case RT_ERR_CUDA: return "RT_ERR_CUDA";
+    case RT_ERR_TIMEOUT: return "RT_ERR_TIMEOUT";
+    case RT_ERR_BOUNDS: return "RT_ERR_BOUNDS";
+    case RT_ERR_NOT_READY: return "RT_ERR_NOT_READY";
+  }
+  return "RT_ERR_UNKNOWN";
+}
+
+rt_status rt_config_default(rt_config* c) {
+  if (c == nullptr) return RT_ERR_INVALID_ARG;
+  c->levels = 16;
+  c->feat_dim = 2;
+  c->log2_T = 19;
+  c->base_res = 16;
+  c->max_res = 2048;
+  c->dense_coarse = 1;
+  c->precision = RT_FP32;
+  c->n_dirs = 128;
+  c->m_dirs = 8;
+  c->brdf_mode = RT_DISNEY;
+  c->near_t = 0.05f;
+  c->far_t = 1.5f;
+  c->f0 = 0.04f;
+  c->force_vis = -1.0f;
+  c->force_vis2 = -1.0f;
+  c->env_h = 64;
+  c->env_w = 128;
+  c->dir_seed = 0x5EED;
+  return RT_OK;
+}
+
+rt_status rt_config_validate(const rt_config* c) {
+  if (c == nullptr) return RT_ERR_INVALID_ARG;
+  const bool ok = c->levels >= 1 && c->levels <= kMaxLevels && c->feat_dim == 2 && c->log2_T >= 8 &&
+                  c->log2_T <= 24 && c->base_res >= 2 && c->max_res >= c->base_res && c->max_res <= (1 << 20) &&
+                  (c->dense_coarse == 0 || c->dense_coarse == 1) &&
+                  (c->precision == RT_FP32 || c->precision == RT_BF16) && c->n_dirs >= 1 && c->n_dirs <= 4096 &&
+                  c->m_dirs >= 1 && c->m_dirs <= 64 && (c->brdf_mode == RT_DISNEY || c->brdf_mode == RT_LAMBERT) &&
+                  std::isfinite(c->near_t) && std::isfinite(c->far_t) && c->near_t >= 0.0f &&
+                  c->far_t > c->near_t && std::isfinite(c->f0) && c->f0 >= 0.0f && c->f0 <= 1.0f &&
+                  !std::isnan(c->force_vis) && c->force_vis <= 1.0f && !std::isnan(c->force_vis2) &&
+                  c->force_vis2 <= 1.0f && c->env_h >= 1 && c->env_h <= 8192 && c->env_w >= 1 &&
+                  c->env_w <= 8192;
+  return ok ? RT_OK : RT_ERR_INVALID_ARG;
+}
+
+int32_t rt_level_resolution(const rt_config* c, int32_t level) {
+  if (rt_config_validate(c) != RT_OK || level < 0 || level >= c->levels) return -1;
+  return level_res(c, level);
+}
+
+int32_t rt_level_is_dense(const rt_config* c, int32_t level) {
+  if (rt_config_validate(c) != RT_OK || level < 0 || level >= c->levels) return -1;
+  return level_dense(c, level_res(c, level)) ? 1 : 0;
+}
+
+int64_t rt_param_count(const rt_config* c, int32_t which) {
+  if (rt_config_validate(c) != RT_OK) return -1;
+  const int64_t lf = (int64_t)c->levels * c->feat_dim;
+  auto mlp = [](int64_t in, int64_t out) { return in * 64 + 64 + 64 * 64 + 64 + 64 * out + out; };
+  switch (which) {
+    case 0: return (int64_t)c->levels * (1LL << c->log2_T) * c->feat_dim;
+    case 1: return mlp(lf, kBrdfOut);
+    case 2: return mlp(lf + kPE, kIrtOut);
+  }
+  return -1;
+}
+
+int64_t rt_workspace_bytes(const rt_config* c) {
+  if (rt_config_validate(c) != RT_OK) return -1;
+  return (int64_t)WPACK_FLOATS * 4 + 256;
+}
+
+rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
+  if (out == nullptr) return RT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (rt_config_validate(cfg) != RT_OK) return RT_ERR_INVALID_ARG;
+  rt_ctx* ctx = new (std::nothrow) rt_ctx{};
+  if (ctx == nullptr) return RT_ERR_OOM;
+  ctx->cfg = *cfg;
+  for (int l = 0; l < cfg->levels; ++l) {
+    ctx->res[l] = level_res(cfg, l);
+    ctx->dense[l] = level_dense(cfg, ctx->res[l]) ? 1 : 0;
+  }
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    delete ctx;
+    return RT_ERR_CUDA;
+  }
+  if (cudaMalloc(&ctx->wpack, (size_t)WPACK_FLOATS * 4) != cudaSuccess) {
+    delete ctx;
+    return RT_ERR_OOM;
+  }
+  if (cudaMalloc(&ctx->status, 256) != cudaSuccess || cudaMemset(ctx->status, 0, 256) != cudaSuccess) {
+    cudaFree(ctx->wpack);
+    delete ctx;
+    return RT_ERR_OOM;
+  }
+  cudaError_t e = rtk::prepare_kernels();
+  if (e != cudaSuccess) {
+    cudaFree(ctx->wpack);
+    cudaFree(ctx->status);
+    delete ctx;
+    return RT_ERR_CUDA;
+  }
+  *out = ctx;
+  return RT_OK;
+}
+
+rt_status rt_destroy(rt_ctx* ctx) {
+  if (ctx == nullptr) return RT_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(ctx->wpack);
+  cudaFree(ctx->status);
+  delete ctx;
+  return cuda_status(e);
+}
+
+rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, const float* irt_w, const float* env,
+                        void* stream) {
+  if (ctx == nullptr || table == nullptr || brdf_w == nullptr || irt_w == nullptr || env == nullptr)
+    return RT_ERR_INVALID_ARG;
+  const uintptr_t ta = ctx->cfg.precision == RT_BF16 ? 4 : 8;
+  if (!aligned(table, ta) || !aligned(brdf_w, 4) || !aligned(irt_w, 4) || !aligned(env, 16))
+    return RT_ERR_INVALID_ARG;
+  ctx->table = table;
+  ctx->env = env;
+  const int lf = ctx->cfg.levels * ctx->cfg.feat_dim;
+  rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, (cudaStream_t)stream));
+  if (st == RT_OK) ctx->ready = true;
+  return st;
+}
+
+rt_status rt_check(rt_ctx* ctx, uint32_t* word, void* stream) {
+  if (ctx == nullptr || word == nullptr) return RT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t h = 0;
+  if (cudaMemcpyAsync(&h, ctx->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return RT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RT_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->status, 0, 4, s) != cudaSuccess) return RT_ERR_CUDA;
+  *word = h;
+  if (h == 0) return RT_OK;
+  return (h >> 28) == 1 ? RT_ERR_TIMEOUT : RT_ERR_BOUNDS;
+}
+
+rt_status rt_encode(rt_ctx* ctx, const float* pos, int64_t P, float* feat, uint32_t* idx, float* w, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (!check_plane(pos) || feat == nullptr || !aligned(feat, 4) || (idx != nullptr && !aligned(idx, 4)) ||
+      (w != nullptr && !aligned(w, 4)))
+    return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_encode(model_desc(ctx), reinterpret_cast<const float4*>(pos), (int)P, feat, idx, w,
+                                   (cudaStream_t)stream));
+}
+
+rt_status rt_decode(rt_ctx* ctx, const float* feat, int64_t P, float* brdf, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (feat == nullptr || !aligned(feat, 4) || brdf == nullptr || !aligned(brdf, 16)) return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_decode(model_desc(ctx), feat, (int)P, brdf, (cudaStream_t)stream));
+}
+
+rt_status rt_trace(rt_ctx* ctx, const float* feat, const float* dirs, int64_t P, int32_t K, float* vis,
+                   float* depth, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || K < 1 || K > 4096) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (feat == nullptr || !aligned(feat, 4) || !check_plane(dirs) || vis == nullptr || !aligned(vis, 4) ||
+      depth == nullptr || !aligned(depth, 4))
+    return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_trace(model_desc(ctx), feat, reinterpret_cast<const float4*>(dirs), (int)P, K, vis,
+                                  depth, (cudaStream_t)stream));
+}
+
+rt_status rt_sample(rt_ctx* ctx, const float* normal, int64_t P, int32_t level, int64_t index_offset, float* dirs,
+                    void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || (level != 0 && level != 1) || index_offset < 0) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (!check_plane(normal) || !check_plane(dirs)) return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_sample(model_desc(ctx), reinterpret_cast<const float4*>(normal), (int)P, level,
+                                   index_offset, reinterpret_cast<float4*>(dirs), (cudaStream_t)stream));
+}
+
+rt_status rt_shade(rt_ctx* ctx, const rt_gbuffer* pts, int64_t P, int32_t level, int64_t index_offset,
+                   const float* vis, const float* lin, float* out, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || (level != 0 && level != 1) || index_offset < 0) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (pts == nullptr || !check_plane(pts->normal) || !check_plane(pts->view) || !check_plane(pts->albedo_rough) ||
+      vis == nullptr || !aligned(vis, 4) || (lin != nullptr && (level == 1 || !aligned(lin, 16))) ||
+      !check_plane(out))
+    return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_shade(model_desc(ctx), *pts, (int)P, level, index_offset, vis,
+                                  reinterpret_cast<const float4*>(lin), reinterpret_cast<float4*>(out),
+                                  (cudaStream_t)stream));
+}
+
+rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, float* radiance,
+                          void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || pixel_offset < 0) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (!check_gbuffer(gb) || !check_plane(radiance)) return RT_ERR_INVALID_ARG;
+  const ModelDesc m = model_desc(ctx);
+  if (ctx->cfg.precision == RT_FP32)
+    return cuda_status(launch_render_fp32(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
+                                          ctx->num_sms, (cudaStream_t)stream));
+  return RT_ERR_UNSUPPORTED;
+}
+
+rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* d_radiance,
+                      float* g_table, float* g_brdf, float* g_irt, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || pixel_offset < 0 || !check_gbuffer(gb) || !check_plane(d_radiance) ||
+      g_table == nullptr || g_brdf == nullptr || g_irt == nullptr)
+    return RT_ERR_INVALID_ARG;
+  (void)stream;
+  return RT_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,311 @@
+// Fused FP32 hot path: stages (a)-(e) of the hash renderer in one persistent
+// kernel (rt_render_frame with precision RT_FP32).
+//
+// Work unit: one warp owns one primary point at a time and walks its N
+// directions in chunks of 32, one direction per lane.  The MLP layers of the
+// chunk are 32 x 64 x K products computed by a register-tiled SIMT GEMM
+// (each lane owns an 8-row x 8-column output tile; weights live in shared
+// memory for the whole kernel).  Activations pass between layers through a
+// per-warp shared buffer laid out k-major with a 4-float pad every 8 rows, so
+// the GEMM operand reads are broadcasts and the epilogue stores are free of
+// bank conflicts.  The per-point reductions over directions are warp
+// shuffles; nothing but the radiance is written to global memory.
+#include "device_common.cuh"
+
+namespace rtk {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kActStride = 64 * 32 + 8 * 4;      // one activation buffer (floats)
+constexpr int kWarpFloats = 2 * kActStride + 96;  // two buffers + primary feature (32) + primary bias (64)
+constexpr size_t kSmemBytes = (size_t)(WPACK_FLOATS + kWarps * kWarpFloats) * sizeof(float);
+
+// element (k, row) of an activation buffer
+__device__ __forceinline__ int aidx(int k, int row) { return k * 32 + (k >> 3) * 4 + row; }
+
+// acc[r][c] += sum_k act(k, 8rg + r) * W[k][8cg + c]
+template <int K>
+__device__ __forceinline__ void warp_gemm(const float* __restrict__ act, const float* __restrict__ W,
+                                          float (&acc)[8][8], int rg, int cg) {
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    const float* ap = act + aidx(k, rg * 8);
+    const float4 a0 = *reinterpret_cast<const float4*>(ap);
+    const float4 a1 = *reinterpret_cast<const float4*>(ap + 4);
+    const float* wp = W + k * 64 + cg * 8;
+    const float4 w0 = *reinterpret_cast<const float4*>(wp);
+    const float4 w1 = *reinterpret_cast<const float4*>(wp + 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], wv[c], acc[r][c]);
+  }
+}
+
+__device__ __forceinline__ void zero(float (&acc)[8][8]) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
+}
+
+// out(col, row) = relu(acc + bias[col])
+__device__ __forceinline__ void store_relu_colbias(float* __restrict__ out, const float (&acc)[8][8],
+                                                   const float* __restrict__ bias, int rg, int cg) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int col = cg * 8 + c;
+    const float b = bias[col];
+    float* o = out + aidx(col, rg * 8);
+    *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][c] + b, 0.f), fmaxf(acc[1][c] + b, 0.f),
+                                                fmaxf(acc[2][c] + b, 0.f), fmaxf(acc[3][c] + b, 0.f));
+    *reinterpret_cast<float4*>(o + 4) = make_float4(fmaxf(acc[4][c] + b, 0.f), fmaxf(acc[5][c] + b, 0.f),
+                                                    fmaxf(acc[6][c] + b, 0.f), fmaxf(acc[7][c] + b, 0.f));
+  }
+}
+
+// out(col, row) = relu(acc + bias[r][c]) (per-row bias held in registers)
+__device__ __forceinline__ void store_relu_tilebias(float* __restrict__ out, const float (&acc)[8][8],
+                                                    const float (&bias)[8][8], int rg, int cg) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int col = cg * 8 + c;
+    float* o = out + aidx(col, rg * 8);
+    *reinterpret_cast<float4*>(o) =
+        make_float4(fmaxf(acc[0][c] + bias[0][c], 0.f), fmaxf(acc[1][c] + bias[1][c], 0.f),
+                    fmaxf(acc[2][c] + bias[2][c], 0.f), fmaxf(acc[3][c] + bias[3][c], 0.f));
+    *reinterpret_cast<float4*>(o + 4) =
+        make_float4(fmaxf(acc[4][c] + bias[4][c], 0.f), fmaxf(acc[5][c] + bias[5][c], 0.f),
+                    fmaxf(acc[6][c] + bias[6][c], 0.f), fmaxf(acc[7][c] + bias[7][c], 0.f));
+  }
+}
+
+// layer 1 over a runtime K (multiple of 8, <= 32)
+__device__ __forceinline__ void warp_gemm_k(const float* act, const float* W, float (&acc)[8][8], int K, int rg,
+                                            int cg) {
+  if (K == 8) warp_gemm<8>(act, W, acc, rg, cg);
+  else if (K == 16) warp_gemm<16>(act, W, acc, rg, cg);
+  else if (K == 24) warp_gemm<24>(act, W, acc, rg, cg);
+  else warp_gemm<32>(act, W, acc, rg, cg);
+}
+
+// write PE(w) of this lane's row and zero rows 27..31
+__device__ __forceinline__ void store_pe(float* act, f3 w, int lane) {
+  positional_encoding(w, [&](int k, float v) { act[aidx(k, lane)] = v; });
+#pragma unroll
+  for (int k = kPE; k < kPEPad; ++k) act[aidx(k, lane)] = 0.0f;
+}
+
+// I's output layer for this lane's row: z = b3 + h2 . W3  (2 outputs)
+__device__ __forceinline__ float2 irt_head(const float* act, const float* sw, int lane) {
+  float z0 = sw[OFF_IB3], z1 = sw[OFF_IB3 + 1];
+#pragma unroll 8
+  for (int k = 0; k < kHidden; ++k) {
+    const float h = act[aidx(k, lane)];
+    const float2 w = *reinterpret_cast<const float2*>(sw + OFF_IW3 + 2 * k);
+    z0 = fmaf(h, w.x, z0);
+    z1 = fmaf(h, w.y, z1);
+  }
+  return make_float2(z0, z1);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, float4* __restrict__ out) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  for (int i = threadIdx.x; i < WPACK_FLOATS / 4; i += kThreads)
+    smem4[i] = __ldg(reinterpret_cast<const float4*>(m.wpack) + i);
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 3, cg = lane & 7;
+  float* actA = sw + WPACK_FLOATS + warp * kWarpFloats;
+  float* actB = actA + kActStride;
+  float* fP = actB + kActStride;   // primary feature, 32 floats
+  float* aP = fP + 32;             // primary layer-1 bias b1 + W1f f, 64 floats
+  const int N = m.N, M = m.M, lfp = m.lfp;
+  const float4* pos4 = reinterpret_cast<const float4*>(gb.pos);
+  const float4* nrm4 = reinterpret_cast<const float4*>(gb.normal);
+  const float4* view4 = reinterpret_cast<const float4*>(gb.view);
+  const float4* ar4 = reinterpret_cast<const float4*>(gb.albedo_rough);
+
+  for (int pix = blockIdx.x * kWarps + warp; pix < P; pix += gridDim.x * kWarps) {
+    const f3 x = xyz(pos4[pix]);
+    const f3 n = xyz(nrm4[pix]);
+    const f3 wo = xyz(view4[pix]);
+    const float4 ar = ar4[pix];
+    const f3 alb = xyz(ar);
+
+    // (a) primary feature: lane 2l and 2l+1 each gather 4 corners of level l
+    {
+      const int l = lane >> 1;
+      float2 part = make_float2(0.f, 0.f);
+      if (l < m.grid.levels) {
+        const int res = m.grid.res[l];
+        uint32_t ix, iy, iz;
+        float wx, wy, wz;
+        grid_cell(x.x, res, ix, wx);
+        grid_cell(x.y, res, iy, wy);
+        grid_cell(x.z, res, iz, wz);
+        const size_t base = (size_t)l << m.grid.log2T;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = (lane & 1) * 4 + cc;
+          const uint32_t row = corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res,
+                                          m.grid.dense[l], m.grid.mask);
+          const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+          const float2 v = table_entry(m.grid, base + row);
+          part.x = fmaf(w, v.x, part.x);
+          part.y = fmaf(w, v.y, part.y);
+        }
+      }
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+      if ((lane & 1) == 0) {
+        fP[lane] = part.x;
+        fP[lane + 1] = part.y;
+      }
+    }
+    __syncwarp();
+    // primary layer-1 bias of I: b1 + W1f . f (shared by all N directions)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      float acc = sw[OFF_IB1 + c];
+      for (int k = 0; k < lfp; ++k) acc = fmaf(fP[k], sw[OFF_IW1F + k * 64 + c], acc);
+      aP[c] = acc;
+    }
+    __syncwarp();
+
+    f3 sum = mk(0.f, 0.f, 0.f);
+    for (int i0 = 0; i0 < N; i0 += 32) {
+      const int i = i0 + lane;
+      const uint64_t q = (uint64_t)(pixel_offset + pix) * (uint64_t)N + (uint64_t)i;
+      const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+
+      // (c) I(f, w_i)
+      float acc[8][8];
+      store_pe(actA, wi, lane);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kPEPad>(actA, sw + OFF_IW1P, acc, rg, cg);
+      store_relu_colbias(actB, acc, aP, rg, cg);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(actB, sw + OFF_IW2, acc, rg, cg);
+      store_relu_colbias(actA, acc, sw + OFF_IB2, rg, cg);
+      __syncwarp();
+      const float2 z = irt_head(actA, sw, lane);
+      const float v = m.force_vis >= 0.f ? m.force_vis : sigmoidf_(z.x);
+      const float t = depth_from_logit(z.y, m.near_t, m.far_t);
+
+      // (d) bounce: x' = x + t w_i, f' = H(x')
+      const f3 x2 = x + wi * t;
+      __syncwarp();
+      for (int l = 0; l < m.grid.levels; ++l) {
+        const float2 f = encode_level(m.grid, l, x2);
+        actA[aidx(2 * l, lane)] = f.x;
+        actA[aidx(2 * l + 1, lane)] = f.y;
+      }
+      for (int k = m.lf; k < lfp; ++k) actA[aidx(k, lane)] = 0.0f;
+      __syncwarp();
+
+      // (b) B(f') layer 1, and I's layer-1 bias for the secondary point
+      zero(acc);
+      warp_gemm_k(actA, sw + OFF_BW1, acc, lfp, rg, cg);
+      store_relu_colbias(actB, acc, sw + OFF_BB1, rg, cg);
+      float a2b[8][8];
+      zero(a2b);
+      warp_gemm_k(actA, sw + OFF_IW1F, a2b, lfp, rg, cg);
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a2b[r][c] += sw[OFF_IB1 + cg * 8 + c];
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(actB, sw + OFF_BW2, acc, rg, cg);
+      store_relu_colbias(actA, acc, sw + OFF_BB2, rg, cg);
+      __syncwarp();
+      float y[7];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) y[o] = sw[OFF_BB3 + o];
+#pragma unroll 4
+      for (int k = 0; k < kHidden; ++k) {
+        const float h = actA[aidx(k, lane)];
+        const float4 w0 = *reinterpret_cast<const float4*>(sw + OFF_BW3 + 8 * k);
+        const float4 w1 = *reinterpret_cast<const float4*>(sw + OFF_BW3 + 8 * k + 4);
+        y[0] = fmaf(h, w0.x, y[0]);
+        y[1] = fmaf(h, w0.y, y[1]);
+        y[2] = fmaf(h, w0.z, y[2]);
+        y[3] = fmaf(h, w0.w, y[3]);
+        y[4] = fmaf(h, w1.x, y[4]);
+        y[5] = fmaf(h, w1.y, y[5]);
+        y[6] = fmaf(h, w1.z, y[6]);
+      }
+      const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+      const f3 n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
+      const f3 a2 = mk(sigmoidf_(y[3]), sigmoidf_(y[4]), sigmoidf_(y[5]));
+      const float r2 = 0.09f + 0.91f * sigmoidf_(y[6]);
+      const f3 wo2 = neg(wi);
+
+      // (c) + (e) at x': M directions about n'
+      f3 lo2 = mk(0.f, 0.f, 0.f);
+      for (int j = 0; j < M; ++j) {
+        const f3 wj = cosine_direction(n2, m.seed, dir_counter(q, M, 1 + j));
+        __syncwarp();
+        store_pe(actA, wj, lane);
+        __syncwarp();
+        zero(acc);
+        warp_gemm<kPEPad>(actA, sw + OFF_IW1P, acc, rg, cg);
+        store_relu_tilebias(actB, acc, a2b, rg, cg);
+        __syncwarp();
+        zero(acc);
+        warp_gemm<kHidden>(actB, sw + OFF_IW2, acc, rg, cg);
+        store_relu_colbias(actA, acc, sw + OFF_IB2, rg, cg);
+        __syncwarp();
+        const float z0 = irt_head(actA, sw, lane).x;
+        const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoidf_(z0);
+        const f3 le = env_lookup(m.env, m.env_h, m.env_w, wj);
+        const f3 fr = brdf_eval(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+        lo2 = lo2 + (le * fr) * v2;
+      }
+      lo2 = lo2 * (kPi / (float)M);
+
+      // Eq. 2 then the primary term of Eq. 1
+      const f3 li = env_lookup(m.env, m.env_h, m.env_w, wi) * v + lo2 * (1.0f - v);
+      const f3 c = li * brdf_eval(alb, ar.w, n, wi, wo, m.f0, m.lambert);
+      if (i < N) sum = sum + c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+      sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+      sum.z += __shfl_xor_sync(0xffffffffu, sum.z, o);
+    }
+    if (lane == 0) {
+      const float sc = kPi / (float)N;
+      out[pix] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t prepare_render_fp32() {
+  return cudaFuncSetAttribute(render_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
+cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset, float4* out,
+                               int num_sms, cudaStream_t s) {
+  const int need = (P + kWarps - 1) / kWarps;
+  const int grid = need < num_sms ? need : num_sms;
+  render_fp32_kernel<<<grid, kThreads, kSmemBytes, s>>>(m, gb, P, offset, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -1,0 +1,80 @@
+// Internal types shared by the host API and the kernels of the GB300 renderer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt.h"
+
+namespace rtk {
+
+constexpr int kMaxLevels = 16;
+constexpr int kHidden = 64;     // width of both MLPs (Sec. 4.1)
+constexpr int kPE = 27;         // [w, sin(2^k pi w), cos(2^k pi w)], k = 0..3
+constexpr int kPEPad = 32;
+constexpr int kBrdfOut = 7;     // [n(3), a(3), r]
+constexpr int kIrtOut = 2;      // [visibility logit, depth logit]
+
+// Packed FP32 weight image (floats).  Weights are stored transposed,
+// [in][out] with out = 64 contiguous, so that one k step of a warp GEMM
+// reads a 64-wide row.  Rows beyond the true fan-in are zero.  The image is
+// copied verbatim into shared memory by the fused kernels.
+constexpr int OFF_IW1F = 0;                      // I, layer 1, feature rows   [32][64]
+constexpr int OFF_IW1P = OFF_IW1F + 32 * 64;     // I, layer 1, PE rows        [32][64]
+constexpr int OFF_IB1 = OFF_IW1P + 32 * 64;      // [64]
+constexpr int OFF_IW2 = OFF_IB1 + 64;            // [64][64]
+constexpr int OFF_IB2 = OFF_IW2 + 64 * 64;       // [64]
+constexpr int OFF_IW3 = OFF_IB2 + 64;            // [64][2]
+constexpr int OFF_IB3 = OFF_IW3 + 64 * 2;        // [2] + 2 pad
+constexpr int OFF_BW1 = OFF_IB3 + 4;             // B, layer 1                 [32][64]
+constexpr int OFF_BB1 = OFF_BW1 + 32 * 64;       // [64]
+constexpr int OFF_BW2 = OFF_BB1 + 64;            // [64][64]
+constexpr int OFF_BB2 = OFF_BW2 + 64 * 64;       // [64]
+constexpr int OFF_BW3 = OFF_BB2 + 64;            // [64][8] (7 + pad)
+constexpr int OFF_BB3 = OFF_BW3 + 64 * 8;        // [8]
+constexpr int WPACK_FLOATS = OFF_BB3 + 8;
+static_assert(OFF_BW1 % 4 == 0 && OFF_BW3 % 4 == 0 && WPACK_FLOATS % 4 == 0, "float4 alignment");
+
+// Hash-grid description passed by value to kernels.
+struct GridDesc {
+  int levels;
+  int log2T;
+  uint32_t mask;               // T - 1
+  int half;                    // 1: table entries are 2 x IEEE half
+  const void* table;           // [L][T][2]
+  int res[kMaxLevels];
+  int dense[kMaxLevels];
+};
+
+// Everything the stage kernels and the fused kernels read besides the G-buffer.
+struct ModelDesc {
+  GridDesc grid;
+  const float* wpack;          // WPACK_FLOATS, device
+  const float4* env;           // [env_h][env_w]
+  int env_h, env_w;
+  int lf;                      // L * F
+  int lfp;                     // lf rounded up to a multiple of 8
+  int N, M;
+  float near_t, far_t, f0;
+  float force_vis, force_vis2;
+  int lambert;
+  uint64_t seed;
+};
+
+// Launch helpers implemented in the .cu files.
+// One-time per-device kernel attributes (large dynamic shared memory); called by rt_create.
+cudaError_t prepare_kernels();
+cudaError_t launch_repack(const float* brdf_w, const float* irt_w, int lf, float* wpack, cudaStream_t s);
+cudaError_t launch_encode(const ModelDesc& m, const float4* pos, int P, float* feat, uint32_t* idx,
+                          float* w, cudaStream_t s);
+cudaError_t launch_decode(const ModelDesc& m, const float* feat, int P, float* brdf, cudaStream_t s);
+cudaError_t launch_trace(const ModelDesc& m, const float* feat, const float4* dirs, int P, int K,
+                         float* vis, float* depth, cudaStream_t s);
+cudaError_t launch_sample(const ModelDesc& m, const float4* normal, int P, int level, long long offset,
+                          float4* dirs, cudaStream_t s);
+cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int level, long long offset,
+                         const float* vis, const float4* lin, float4* out, cudaStream_t s);
+cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
+                               float4* out, int num_sms, cudaStream_t s);
+
+}  // namespace rtk

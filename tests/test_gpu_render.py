@@ -1,0 +1,117 @@
+"""Parity of the fused rt_render_frame (FP32) with the FP64 oracle, and its edge cases."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+from oracle import render as orender
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_10327_gb300 import build
+    build.build()
+    from paper_2409_10327_gb300 import binding
+    return binding
+
+
+def _render(cfg, sc, gb, offset=0, **ov):
+    r = helpers.renderer_for(cfg, sc, **ov)
+    out = r.render_frame(helpers.to_cuda(gb), pixel_offset=offset)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _parity(cfg, sc, gb, out, offset=0, rows=None, **modes):
+    prm = helpers.oracle_params(sc)
+    opt = helpers.oracle_options(cfg, **modes)
+    ref = orender.render(gb, prm, opt, pixel_offset=offset, rows=rows)
+    sens = orender.float32_sensitivity(gb, prm, opt, pixel_offset=offset, rows=rows, draws=4)
+    got = out[:, :3] if rows is None else out[rows, :3]
+    ok, stats = helpers.fp32_parity(got, ref, sens)
+    assert ok, stats
+    return stats
+
+
+@pytest.mark.parametrize("mode", [{}, {"force_vis": 0.0}, {"lambert": True}])
+def test_tiny_frame_matches_oracle(lib, mode):
+    cfg = scenegen.CONFIGS["tiny64"]
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    ov = {"force_vis": mode["force_vis"]} if "force_vis" in mode else {}
+    if mode.get("lambert"):
+        ov["brdf_mode"] = 1
+    out = _render(cfg, sc, gb, **ov)
+    assert np.all(out[:, 3] == 0)
+    _parity(cfg, sc, gb, out, **mode)
+
+
+def test_white_furnace(lib):
+    cfg = helpers.small_cfg(n_dirs=64)
+    sc, gb = helpers.scene_arrays(cfg, 1)
+    sc.env[..., :3] = 1.0
+    out = _render(cfg, sc, gb, force_vis=1.0, brdf_mode=1)
+    np.testing.assert_allclose(out[:, :3], gb["albedo_rough"][:, :3], rtol=2e-6)
+
+
+def test_fully_occluded_is_black(lib):
+    cfg = helpers.small_cfg()
+    sc, gb = helpers.scene_arrays(cfg, 1)
+    out = _render(cfg, sc, gb, force_vis=0.0, force_vis2=0.0)
+    assert np.all(out == 0.0)
+
+
+@pytest.mark.parametrize("n_dirs,m_dirs,levels,log2_T,P", [(40, 3, 5, 12, 37), (7, 1, 1, 10, 5), (96, 8, 16, 19, 19),
+                                                          (33, 16, 3, 9, 64)])
+def test_ragged_shapes_match_oracle(lib, n_dirs, m_dirs, levels, log2_T, P):
+    cfg = helpers.small_cfg(n_dirs=n_dirs, m_dirs=m_dirs, levels=levels, log2_T=log2_T,
+                            max_res=256 if levels > 1 else 16)
+    sc, gb = helpers.scene_arrays(cfg, 3, bias=0.2, n_pixels=P)
+    out = _render(cfg, sc, gb, offset=1000)
+    _parity(cfg, sc, gb, out, offset=1000)
+
+
+def test_sharded_frame_is_bit_identical(lib):
+    cfg = helpers.small_cfg()
+    sc, gb = helpers.scene_arrays(cfg, 5, n_pixels=300)
+    r = helpers.renderer_for(cfg, sc)
+    dgb = helpers.to_cuda(gb)
+    whole = r.render_frame(dgb).cpu().numpy()
+    parts = []
+    for lo, hi in [(0, 100), (100, 101), (101, 300)]:
+        parts.append(r.render_frame({k: v[lo:hi].contiguous() for k, v in dgb.items()}, pixel_offset=lo).cpu().numpy())
+    np.testing.assert_array_equal(np.concatenate(parts), whole)
+
+
+def test_empty_frame_and_errors(lib):
+    cfg = helpers.small_cfg()
+    sc, gb = helpers.scene_arrays(cfg, 0, n_pixels=4)
+    r = helpers.renderer_for(cfg, sc)
+    empty = {k: torch.zeros(0, 4, device="cuda") for k in gb}
+    assert r.render_frame(empty).shape == (0, 4)
+    dgb = helpers.to_cuda(gb)
+    bad = dict(dgb)
+    bad["pos"] = torch.zeros(4 * 4 + 1, device="cuda")[1:].view(4, 4)   # misaligned plane
+    with pytest.raises(lib.RtError) as e:
+        r.render_frame(bad)
+    assert e.value.status == lib.RT_ERR_INVALID_ARG
+    fresh = lib.Renderer(lib.make_config(cfg))
+    with pytest.raises(lib.RtError) as e:
+        fresh.render_frame(dgb)
+    assert e.value.status == lib.RT_ERR_NOT_READY
+    assert r.check() == 0
+
+
+def test_full_size_frame_sampled_against_oracle(lib):
+    # the 800x800, N=128, M=8, L=16, T=2^19 workload in the bench's launch
+    # configuration, checked on a seeded sample of its pixels
+    cfg = scenegen.CONFIGS["frame800"]
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    out = _render(cfg, sc, gb)
+    rows = scenegen.subset_permutation(cfg.n_pixels, 48, seed=0)
+    assert np.isfinite(out).all()
+    _parity(cfg, sc, gb, out, rows=rows)
