@@ -286,9 +286,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pixels", type=int, default=0,
+                    help="render only the first P pixel rows of each frame (a smaller case for profilers)")
     args = ap.parse_args()
     import dataclasses
     cfg = dataclasses.replace(scenegen.CONFIGS[args.config], precision=args.precision)
+    if args.pixels:
+        cfg = dataclasses.replace(cfg, name=cfg.name + f"[{args.pixels} px]", width=args.pixels, height=1)
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

@@ -40,17 +40,30 @@ def as_layers(layers) -> List[Tuple[torch.Tensor, torch.Tensor]]:
             for w, b in layers]
 
 
-def mlp3(z: torch.Tensor, layers: Layers) -> torch.Tensor:
-    """Three linear layers with ReLU after the first two."""
+def _jit(x: torch.Tensor, jitter) -> torch.Tensor:
+    """Conditioning probe only: x (1 + rel z), z ~ N(0, 1) from generator g."""
+    if jitter is None:
+        return x
+    rel, g = jitter
+    return x * (1.0 + rel * torch.randn(x.shape, generator=g, dtype=x.dtype))
+
+
+def mlp3(z: torch.Tensor, layers: Layers, jitter=None) -> torch.Tensor:
+    """Three linear layers with ReLU after the first two.
+
+    `jitter` = (rel, torch.Generator) perturbs the input and both hidden
+    activations by relative Gaussian noise; it is used only by the
+    conditioning probe ``render.float32_sensitivity``.
+    """
     (w1, b1), (w2, b2), (w3, b3) = layers
-    h1 = torch.relu(z @ w1.T + b1)
-    h2 = torch.relu(h1 @ w2.T + b2)
-    return h2 @ w3.T + b3
+    h1 = torch.relu(_jit(z, jitter) @ w1.T + b1)
+    h2 = torch.relu(_jit(h1, jitter) @ w2.T + b2)
+    return _jit(h2, jitter) @ w3.T + b3
 
 
-def brdf_decoder(f: torch.Tensor, layers: Layers):
+def brdf_decoder(f: torch.Tensor, layers: Layers, jitter=None):
     """a, r, n = B(f): albedo [.,3], roughness [.], unit normal [.,3]."""
-    y = mlp3(f, layers)
+    y = mlp3(f, layers, jitter)
     n = y[:, 0:3]
     n = n / n.norm(dim=1, keepdim=True).clamp(min=1e-12)
     a = torch.sigmoid(y[:, 3:6])
@@ -74,9 +87,9 @@ def depth_from_logit(t_hat: torch.Tensor, near: float, far: float) -> torch.Tens
 
 
 def implicit_ray_tracer(f: torch.Tensor, w: torch.Tensor, layers: Layers,
-                        near: float, far: float):
+                        near: float, far: float, jitter=None):
     """v, t = I(f, w): soft visibility in (0, 1) and expected depth in [near, far]."""
-    y = mlp3(torch.cat([f, positional_encoding(w)], dim=-1), layers)
+    y = mlp3(torch.cat([f, positional_encoding(w)], dim=-1), layers, jitter)
     v = torch.sigmoid(y[:, 0])
     t = depth_from_logit(torch.nn.functional.softplus(y[:, 1]), near, far)
     return v, t

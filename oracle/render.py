@@ -65,6 +65,7 @@ class Options:
     # strongly the exact result reacts to float32-sized rounding of x'.
     x2_jitter: float = 0.0
     s_jitter: float = 0.0        # absolute jitter of the sphere points s of both samplers
+    mlp_jitter: float = 0.0      # relative jitter of MLP inputs and hidden activations
     jitter_seed: int = 0
 
     @staticmethod
@@ -110,6 +111,10 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # (a) primary feature
     f = hashgrid.encode(x, prm.table, res, dense)
+    jit = None
+    if opt.mlp_jitter > 0:
+        g = torch.Generator().manual_seed(int(opt.jitter_seed) * 1000003 + int(np.asarray(global_ids)[0]))
+        jit = (opt.mlp_jitter, g)
 
     # primary directions, slot 0 of sample q = gid * N + i
     q = np.asarray(global_ids, np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
@@ -118,7 +123,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
-    v, t = mlp.implicit_ray_tracer(f_rep, w_i.reshape(P * N, 3), prm.irt, opt.near, opt.far)
+    v, t = mlp.implicit_ray_tracer(f_rep, w_i.reshape(P * N, 3), prm.irt, opt.near, opt.far, jit)
     if opt.force_vis >= 0:
         v = torch.full_like(v, opt.force_vis)
 
@@ -127,7 +132,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     if opt.x2_jitter > 0:
         x2 = x2 * (1.0 + opt.x2_jitter * _noise(opt, global_ids, 2, (N, 3)))
     f2 = hashgrid.encode(x2.reshape(P * N, 3), prm.table, res, dense)
-    a2, r2, n2 = mlp.brdf_decoder(f2, prm.brdf)                           # (b)
+    a2, r2, n2 = mlp.brdf_decoder(f2, prm.brdf, jit)                      # (b)
 
     # secondary directions, slots 1..M about the (detached) secondary normal
     if fixed_dirs is None:
@@ -138,7 +143,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     else:
         w_j = fixed_dirs
     f2_rep = f2[:, None, :].expand(P * N, M, f2.shape[1]).reshape(P * N * M, -1)
-    v2, _ = mlp.implicit_ray_tracer(f2_rep, w_j.reshape(-1, 3), prm.irt, opt.near, opt.far)
+    v2, _ = mlp.implicit_ray_tracer(f2_rep, w_j.reshape(-1, 3), prm.irt, opt.near, opt.far, jit)
     v2 = v2.reshape(P * N, M)
     if opt.force_vis2 >= 0:
         v2 = torch.full_like(v2, opt.force_vis2)
@@ -191,7 +196,8 @@ def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: i
 
 
 def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
-                        rows: Optional[np.ndarray] = None, rel: float = 2.0 ** -23, draws: int = 2) -> np.ndarray:
+                        rows: Optional[np.ndarray] = None, rel: float = 2.0 ** -23, draws: int = 2,
+                        mlp: bool = False) -> np.ndarray:
     """Per-pixel, per-channel max |L(jittered) - L| over `draws` float32-sized jitters.
 
     Two inputs of the exact result are ill-conditioned at float32 scale:
@@ -202,14 +208,34 @@ def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pi
     can move by far more than 1e-4 when x' or s changes by one float32
     rounding.  This probe jitters x' (relative) and s (absolute) by `rel`
     and reports how far the exact result moves; the FP32 parity tests scale
-    their per-pixel bound by it.
+    their per-pixel bound by it.  With mlp=True it also jitters the MLP inputs
+    and hidden activations (per sample) and both hidden weight matrices (per
+    draw) by `rel`, and the table by 2^-11: the roundings of a bf16 MLP with
+    an FP16 table, used by the BF16 tests.
     """
     base = render(gb, prm, opt, pixel_offset, rows)
     worst = np.zeros_like(base)
     for d in range(draws):
-        o = dataclasses.replace(opt, x2_jitter=rel, s_jitter=rel, jitter_seed=1 + d)
-        worst = np.maximum(worst, np.abs(render(gb, prm, o, pixel_offset, rows) - base))
+        o = dataclasses.replace(opt, x2_jitter=rel, s_jitter=rel, mlp_jitter=rel if mlp else 0.0, jitter_seed=1 + d)
+        p = _perturbed_weights(prm, rel, 1 + d) if mlp else prm
+        worst = np.maximum(worst, np.abs(render(gb, p, o, pixel_offset, rows) - base))
     return worst
+
+
+def _perturbed_weights(prm: Params, rel: float, seed: int) -> Params:
+    """Params with both hidden layers' weight matrices scaled by (1 + rel z) and the
+    table by (1 + 2^-11 z): the systematic part of bf16 weights and an FP16 table."""
+    g = torch.Generator().manual_seed(seed)
+
+    def jw(layers):
+        out = []
+        for k, (w, b) in enumerate(layers):
+            if k < 2:
+                w = w * (1.0 + rel * torch.randn(w.shape, generator=g, dtype=w.dtype))
+            out.append((w, b))
+        return out
+    table = prm.table * (1.0 + 2.0 ** -11 * torch.randn(prm.table.shape, generator=g, dtype=prm.table.dtype))
+    return Params(table, jw(prm.brdf), jw(prm.irt), prm.env)
 
 
 def distill_loss(gb, rows, student: Params, target: torch.Tensor, opt: Options,

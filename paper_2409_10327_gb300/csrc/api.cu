@@ -16,6 +16,7 @@ struct rt_ctx {
   int res[kMaxLevels];
   int dense[kMaxLevels];
   float* wpack;        // WPACK_FLOATS
+  uint8_t* wbf16;      // WBF16_BYTES
   uint32_t* status;    // device status word
   const void* table;
   const float* env;
@@ -53,6 +54,8 @@ ModelDesc model_desc(const rt_ctx* ctx) {
     m.grid.dense[l] = l < c.levels ? ctx->dense[l] : 0;
   }
   m.wpack = ctx->wpack;
+  m.wbf16 = ctx->wbf16;
+  m.status = ctx->status;
   m.env = reinterpret_cast<const float4*>(ctx->env);
   m.env_h = c.env_h;
   m.env_w = c.env_w;
@@ -165,7 +168,7 @@ int64_t rt_param_count(const rt_config* c, int32_t which) {
 
 int64_t rt_workspace_bytes(const rt_config* c) {
   if (rt_config_validate(c) != RT_OK) return -1;
-  return (int64_t)WPACK_FLOATS * 4 + 256;
+  return (int64_t)WPACK_FLOATS * 4 + WBF16_BYTES + 256;
 }
 
 rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
@@ -188,14 +191,21 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
     delete ctx;
     return RT_ERR_OOM;
   }
+  if (cudaMalloc(&ctx->wbf16, (size_t)WBF16_BYTES) != cudaSuccess) {
+    cudaFree(ctx->wpack);
+    delete ctx;
+    return RT_ERR_OOM;
+  }
   if (cudaMalloc(&ctx->status, 256) != cudaSuccess || cudaMemset(ctx->status, 0, 256) != cudaSuccess) {
     cudaFree(ctx->wpack);
+    cudaFree(ctx->wbf16);
     delete ctx;
     return RT_ERR_OOM;
   }
   cudaError_t e = rtk::prepare_kernels();
   if (e != cudaSuccess) {
     cudaFree(ctx->wpack);
+    cudaFree(ctx->wbf16);
     cudaFree(ctx->status);
     delete ctx;
     return RT_ERR_CUDA;
@@ -208,6 +218,7 @@ rt_status rt_destroy(rt_ctx* ctx) {
   if (ctx == nullptr) return RT_OK;
   cudaError_t e = cudaDeviceSynchronize();
   cudaFree(ctx->wpack);
+  cudaFree(ctx->wbf16);
   cudaFree(ctx->status);
   delete ctx;
   return cuda_status(e);
@@ -224,6 +235,7 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
   ctx->env = env;
   const int lf = ctx->cfg.levels * ctx->cfg.feat_dim;
   rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, (cudaStream_t)stream));
+  if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, (cudaStream_t)stream));
   if (st == RT_OK) ctx->ready = true;
   return st;
 }
@@ -311,7 +323,9 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
   if (ctx->cfg.precision == RT_FP32)
     return cuda_status(launch_render_fp32(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
                                           ctx->num_sms, (cudaStream_t)stream));
-  return RT_ERR_UNSUPPORTED;
+  if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;   // the BF16 tile holds at most 33 pixels
+  return cuda_status(launch_render_bf16(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
+                                        ctx->num_sms, (cudaStream_t)stream));
 }
 
 rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* d_radiance,

@@ -1,0 +1,576 @@
+// Fused BF16 tensor-core hot path: stages (a)-(e) of the hash renderer in one
+// persistent kernel (rt_render_frame with precision RT_BF16).
+//
+// Layout of the work.  A CTA holds two independent warpgroups.  Each
+// warpgroup owns a contiguous range of primary points and walks its
+// secondary samples (point p, direction i) in tiles of 128 consecutive
+// samples: thread t of the warpgroup owns row t of the tile, which is also
+// TMEM lane t of the warpgroup's accumulators.  Every MLP layer of the tile
+// is one chain of tcgen05.mma (M = 128, N = 64 or 16, K = 16 per
+// instruction) issued by one thread, with the A operand (activations, bf16)
+// and the B operand (weights, bf16) in 128-byte-swizzled shared memory and
+// the FP32 accumulator in tensor memory.  The epilogue reads the accumulator
+// with tcgen05.ld, adds the bias, applies ReLU and rounds to bf16 for the
+// next layer.  Hash interpolation, depth, shading and all sums stay in FP32;
+// the table is read as FP16.
+//
+// Per tile: I on [f, PE(w_i)], the bounce and f' = H(x'), B on f', then for
+// each of the M secondary directions I on [f', PE(w'_j)] with f' kept in the
+// A tile, then Eq. 1 / Eq. 2 and a deterministic segmented reduction of the
+// rows into their pixels.  The two 64-wide layers of each MLP run on the
+// tensor cores; the narrow output layer (2 or 7 outputs) runs in FP32 on
+// the CUDA cores straight from the FP32 layer-2 accumulator, which saves a
+// round trip per MLP and keeps t and n' free of one bf16 rounding.
+//
+// Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
+// warpgroup records kStatusTimeout in the status word and stops.
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+
+namespace rtk {
+
+// ---- BF16 weight image (runs after the FP32 repack on the same stream) -----
+__global__ void repack_bf16_kernel(const float* __restrict__ wp, uint8_t* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // one element of a 64-wide row
+  const int total_rows = 64 + 64 + 16 + 64 + 64 + 16;
+  if (e >= total_rows * 64) return;
+  const int row = e / 64, k = e % 64;
+  float v = 0.0f;
+  int base, n;
+  if (row < 64) {                     // I layer 1: [f | PE]
+    base = OFFB_IW1; n = row;
+    v = k < 32 ? wp[OFF_IW1F + k * 64 + n] : wp[OFF_IW1P + (k - 32) * 64 + n];
+  } else if (row < 128) {
+    base = OFFB_IW2; n = row - 64;
+    v = wp[OFF_IW2 + k * 64 + n];
+  } else if (row < 144) {
+    base = OFFB_IW3; n = row - 128;
+    v = n < 2 ? wp[OFF_IW3 + k * 2 + n] : 0.0f;
+  } else if (row < 208) {
+    base = OFFB_BW1; n = row - 144;
+    v = k < 32 ? wp[OFF_BW1 + k * 64 + n] : 0.0f;
+  } else if (row < 272) {
+    base = OFFB_BW2; n = row - 208;
+    v = wp[OFF_BW2 + k * 64 + n];
+  } else {
+    base = OFFB_BW3; n = row - 272;
+    v = n < 7 ? wp[OFF_BW3 + k * 8 + n] : 0.0f;
+  }
+  *reinterpret_cast<__nv_bfloat16*>(out + base + swz128(n, k)) = __float2bfloat16_rn(v);
+}
+
+cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s) {
+  repack_bf16_kernel<<<(288 * 64 + 255) / 256, 256, 0, s>>>(wpack, wbf16);
+  return cudaGetLastError();
+}
+
+namespace {
+
+constexpr int kWG = 2;                       // warpgroups per CTA
+constexpr int kThreadsB = 128 * kWG;
+constexpr int kTmemCols = 256;               // 128 per warpgroup: D1 = [0, 64), D2 = [64, 128)
+constexpr int kPixSlots = 34;                // pixels touched by one tile when N >= 4
+// shared-memory layout (offsets from a 1024-aligned base)
+constexpr int SM_W = 0;
+constexpr int WG_X = 0;                      // A tile [128][64] bf16, swizzled
+constexpr int WG_H = 16384;                  // hidden activations [128][64] bf16, swizzled
+constexpr int WG_FPIX = 32768;               // primary features [34][32] bf16; reused as red[128] float4
+constexpr int WG_MISC = WG_FPIX + 2560;      // mbarrier (8), carry (16)
+constexpr int WG_BYTES = 35840;
+constexpr int SM_WG = WBF16_BYTES;
+constexpr int SM_BIAS = SM_WG + kWG * WG_BYTES;          // FP32 biases
+// FP32 biases, then the FP32 output layers (I: W3 [64][2], B: W3 [64][8]) that
+// the epilogues evaluate on the CUDA cores from the FP32 layer-2 accumulator
+constexpr int BI_IB1 = 0, BI_IB2 = 64, BI_IB3 = 128, BI_BB1 = 132, BI_BB2 = 196, BI_BB3 = 260;
+constexpr int BI_IW3 = 268, BI_BW3 = BI_IW3 + 128, BI_N = BI_BW3 + 512;
+constexpr int SM_TMEMSLOT = SM_BIAS + BI_N * 4;
+constexpr int SM_BYTES = SM_TMEMSLOT + 16;
+constexpr size_t kSmemAlloc = SM_BYTES + 1024;
+static_assert(WG_MISC + 64 <= WG_BYTES, "warpgroup block overflow");
+static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
+
+constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t kIdescN64 = idesc_bf16(128, 64);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: true when the phase completed, false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, phase)) return true;
+    if (globaltimer() - t0 > 2000000000ull) return false;
+  }
+}
+
+// Warpgroup barrier (named barrier 1 + wg) that also ORs a flag across the group.
+__device__ __forceinline__ int wg_sync_or(int wg, int v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, 128, p;\n"
+      " selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v), "r"(wg + 1)
+      : "memory");
+  return r;
+}
+__device__ __forceinline__ void wg_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ void st_chunk(uint8_t* tile, int row, int chunk, uint32_t a, uint32_t b, uint32_t c,
+                                         uint32_t d) {
+  *reinterpret_cast<uint4*>(tile + row * 128 + ((chunk ^ (row & 7)) << 4)) = make_uint4(a, b, c, d);
+}
+
+// D <- A[128 x 16*ksteps] . B[N x 16*ksteps]^T
+__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_s, uint32_t b_s, int ksteps, uint32_t idesc) {
+  for (int k = 0; k < ksteps; ++k) mma_bf16(d, sdesc(a_s + 32 * k), sdesc(b_s + 32 * k), idesc, k > 0 ? 1u : 0u);
+}
+
+// hidden epilogue: H[row] = bf16(relu(D[row][0:64] + bias))
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bias, uint8_t* H, int row) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t r[32];
+    tmem_ld32(taddr + 32 * h, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      uint32_t q[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = 32 * h + 8 * c + 2 * e;
+        q[e] = pack_relu_bf16(__uint_as_float(r[8 * c + 2 * e]) + bias[col],
+                              __uint_as_float(r[8 * c + 2 * e + 1]) + bias[col + 1]);
+      }
+      st_chunk(H, row, 4 * h + c, q[0], q[1], q[2], q[3]);
+    }
+  }
+}
+
+// Output layer in FP32: z[o] = b3[o] + sum_k relu(D[row][k] + b2[k]) W3[k][o]
+template <int NOUT, int LDW>
+__device__ __forceinline__ void head_fp32(uint32_t taddr, const float* b2, const float* W3, const float* b3,
+                                          float (&z)[NOUT]) {
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) z[o] = b3[o];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t r[32];
+    tmem_ld32(taddr + 32 * h, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaxf(__uint_as_float(r[k]) + b2[32 * h + k], 0.0f);
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) z[o] = fmaf(a, W3[(32 * h + k) * LDW + o], z[o]);
+    }
+  }
+}
+
+// f' = H(x') as 16 packed bf16 pairs (zero beyond L levels).  The gathers of
+// kEncBatch levels (8 loads each) are issued before any of them is consumed,
+// so a thread waits on the L2 16 / kEncBatch times per point instead of 16.
+constexpr int kEncBatch = 2;
+__device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint32_t (&fq)[16]) {
+#pragma unroll
+  for (int l0 = 0; l0 < kMaxLevels; l0 += kEncBatch) {
+    uint32_t v[kEncBatch][8];   // raw half2 table entries (the BF16 path always reads an FP16 table)
+    float w[kEncBatch][3];
+#pragma unroll
+    for (int b = 0; b < kEncBatch; ++b) {
+      const int l = l0 + b;
+      if (l < g.levels) {
+        const int res = g.res[l];
+        uint32_t ix, iy, iz;
+        grid_cell(x.x, res, ix, w[b][0]);
+        grid_cell(x.y, res, iy, w[b][1]);
+        grid_cell(x.z, res, iz, w[b][2]);
+        const size_t base = (size_t)l << g.log2T;
+        const uint32_t* tab = reinterpret_cast<const uint32_t*>(g.table) + base;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          v[b][c] = __ldg(tab + corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res, g.dense[l],
+                                           g.mask));
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kEncBatch; ++b) {
+      const int l = l0 + b;
+      float f0 = 0.f, f1 = 0.f;
+      if (l < g.levels) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float wt = ((c & 1) ? w[b][0] : 1.0f - w[b][0]) * ((c & 2) ? w[b][1] : 1.0f - w[b][1]) *
+                           ((c & 4) ? w[b][2] : 1.0f - w[b][2]);
+          const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[b][c]));
+          f0 = fmaf(wt, e.x, f0);
+          f1 = fmaf(wt, e.y, f1);
+        }
+      }
+      fq[l] = pack_bf16(f0, f1);
+    }
+  }
+}
+
+// PE(w) as bf16 into chunks 4..7 of the A tile row (27 values, then zeros)
+__device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
+  float pe[32];
+  positional_encoding(w, [&](int k, float v) { pe[k] = v; });
+#pragma unroll
+  for (int k = kPE; k < 32; ++k) pe[k] = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    st_chunk(X, row, 4 + c, pack_bf16(pe[8 * c], pe[8 * c + 1]), pack_bf16(pe[8 * c + 2], pe[8 * c + 3]),
+             pack_bf16(pe[8 * c + 4], pe[8 * c + 5]), pack_bf16(pe[8 * c + 6], pe[8 * c + 7]));
+}
+
+__global__ void __launch_bounds__(kThreadsB, 2)
+render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, float4* __restrict__ out) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x;
+  const int wg = tid >> 7, t = tid & 127, warp = t >> 5, lane = t & 31;
+  uint8_t* Wsm = sm + SM_W;
+  uint8_t* wgb = sm + SM_WG + wg * WG_BYTES;
+  uint8_t* X = wgb + WG_X;
+  uint8_t* H = wgb + WG_H;
+  uint8_t* fpix = wgb + WG_FPIX;
+  float4* red = reinterpret_cast<float4*>(wgb + WG_FPIX);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WG_MISC);
+  float4* carry_s = reinterpret_cast<float4*>(wgb + WG_MISC + 16);
+  float* bias = reinterpret_cast<float*>(sm + SM_BIAS);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SM_TMEMSLOT);
+
+  // ---- CTA set-up: weights and biases into shared memory, TMEM, barriers
+  for (int i = tid; i < WBF16_BYTES / 16; i += kThreadsB)
+    reinterpret_cast<uint4*>(Wsm)[i] = __ldg(reinterpret_cast<const uint4*>(m.wbf16) + i);
+  for (int i = tid; i < BI_N; i += kThreadsB) {
+    float v = 0.0f;
+    if (i < 64) v = m.wpack[OFF_IB1 + i];
+    else if (i < 128) v = m.wpack[OFF_IB2 + i - 64];
+    else if (i < 130) v = m.wpack[OFF_IB3 + i - 128];
+    else if (i >= BI_BB1 && i < BI_BB1 + 64) v = m.wpack[OFF_BB1 + i - BI_BB1];
+    else if (i >= BI_BB2 && i < BI_BB2 + 64) v = m.wpack[OFF_BB2 + i - BI_BB2];
+    else if (i >= BI_BB3 && i < BI_BB3 + 7) v = m.wpack[OFF_BB3 + i - BI_BB3];
+    else if (i >= BI_IW3 && i < BI_IW3 + 128) v = m.wpack[OFF_IW3 + i - BI_IW3];
+    else if (i >= BI_BW3) v = m.wpack[OFF_BW3 + i - BI_BW3];
+    bias[i] = v;
+  }
+  if (t == 0) {
+    mbar_init(smem_u32(bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  if (warp == 0 && wg == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot + (uint32_t)(128 * wg);
+  const uint32_t D1 = tmem, D2 = tmem + 64;
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const uint32_t bar_a = smem_u32(bar);
+  const uint32_t X_s = smem_u32(X), H_s = smem_u32(H), W_s = smem_u32(Wsm);
+
+  const int N = m.N, M = m.M;
+  const float4* pos4 = reinterpret_cast<const float4*>(gb.pos);
+  const float4* nrm4 = reinterpret_cast<const float4*>(gb.normal);
+  const float4* view4 = reinterpret_cast<const float4*>(gb.view);
+  const float4* ar4 = reinterpret_cast<const float4*>(gb.albedo_rough);
+
+  const long long workers = (long long)gridDim.x * kWG;
+  const long long worker = (long long)blockIdx.x * kWG + wg;
+  const long long p0 = (long long)P * worker / workers, p1 = (long long)P * (worker + 1) / workers;
+  const long long s_end = p1 * N;
+  uint32_t phase = 0;
+  int abort = 0;
+  if (t == 0) *carry_s = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  // One MMA round trip: barrier with an abort vote, issue by thread 0,
+  // commit, bounded wait.  A wait that gives up only raises `abort`; the
+  // vote at the next round trip then stops all 128 threads together, so the
+  // warpgroup never splits across barriers.
+  uint32_t pending_phase = 0;
+  auto run_mma = [&](auto issue) -> bool {
+    fence_async_smem();
+    tc_fence_before();
+    abort = wg_sync_or(wg, abort);
+    if (abort) return false;
+    if (t == 0) {
+      tc_fence_after();
+      issue();
+      mma_commit(bar_a);
+    }
+    if (!mbar_wait(bar_a, phase)) {
+      if (!abort && t == 0) atomicOr(m.status, kStatusTimeout | 1u);
+      abort = 1;
+      pending_phase = phase;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    return true;
+  };
+
+  for (long long sbase = p0 * N; sbase < s_end; sbase += 128) {
+    const long long p_first = sbase / N;
+    const int off0 = (int)(sbase - p_first * N);
+    const int nvalid = (int)min(128LL, s_end - sbase);
+    const int npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
+    const bool valid = t < nvalid;
+    const int local = off0 + (valid ? t : nvalid - 1);
+    const int ps = local / N;
+    const int i = local - ps * N;
+    const long long p = p_first + ps;
+
+    // (a) primary features of the tile's pixels, 32 threads per pixel (2 per level)
+    for (int g = 0; g < npix; g += 4) {
+      const int slot = g + warp;
+      float2 part = make_float2(0.f, 0.f);
+      const int l = lane >> 1;
+      if (slot < npix && l < m.grid.levels) {
+        const f3 xs = xyz(pos4[p_first + slot]);
+        const int res = m.grid.res[l];
+        uint32_t ix, iy, iz;
+        float wx, wy, wz;
+        grid_cell(xs.x, res, ix, wx);
+        grid_cell(xs.y, res, iy, wy);
+        grid_cell(xs.z, res, iz, wz);
+        const size_t base = (size_t)l << m.grid.log2T;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = (lane & 1) * 4 + cc;
+          const uint32_t row = corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res,
+                                          m.grid.dense[l], m.grid.mask);
+          const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+          const float2 v = table_entry(m.grid, base + row);
+          part.x = fmaf(w, v.x, part.x);
+          part.y = fmaf(w, v.y, part.y);
+        }
+      }
+      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+      if (slot < npix && (lane & 1) == 0)
+        *reinterpret_cast<uint32_t*>(fpix + slot * 64 + 2 * lane) = pack_bf16(part.x, part.y);
+    }
+    wg_sync(wg);
+
+    const f3 x = xyz(pos4[p]);
+    const f3 n = xyz(nrm4[p]);
+    const f3 wo = xyz(view4[p]);
+    const float4 ar = ar4[p];
+    const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
+    const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+    // Eq. 1 factors of the primary direction, fetched before the MMAs so the
+    // env-map loads overlap them
+    const f3 le1 = env_lookup(m.env, m.env_h, m.env_w, wi);
+    const f3 fr1 = brdf_eval(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 v = src[c];
+        st_chunk(X, t, c, v.x, v.y, v.z, v.w);
+      }
+    }
+    store_pe_bf16(X, t, wi);
+
+    // (c) I(f, w_i)
+    if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); })) break;
+    epilogue_hidden(D1 + lane_off, bias + BI_IB1, H, t);
+    if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); })) break;
+    float v, tdep;
+    {
+      float z[2];
+      head_fp32<2, 2>(D2 + lane_off, bias + BI_IB2, bias + BI_IW3, bias + BI_IB3, z);
+      v = m.force_vis >= 0.f ? m.force_vis : sigmoidf_(z[0]);
+      tdep = depth_from_logit(z[1], m.near_t, m.far_t);
+    }
+
+    // (d) bounce: x' = x + t w_i; f' = H(x') into chunks 0..3 of the A tile
+    {
+      const f3 x2 = x + wi * tdep;
+      uint32_t fq[16];
+      encode_point_bf16(m.grid, x2, fq);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) st_chunk(X, t, c, fq[4 * c], fq[4 * c + 1], fq[4 * c + 2], fq[4 * c + 3]);
+    }
+
+    // (b) B(f')
+    if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_BW1, 2, kIdescN64); })) break;
+    epilogue_hidden(D1 + lane_off, bias + BI_BB1, H, t);
+    if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_BW2, 4, kIdescN64); })) break;
+    f3 n2, a2;
+    float r2;
+    {
+      float y[7];
+      head_fp32<7, 8>(D2 + lane_off, bias + BI_BB2, bias + BI_BW3, bias + BI_BB3, y);
+      const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+      n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
+      a2 = mk(sigmoidf_(y[3]), sigmoidf_(y[4]), sigmoidf_(y[5]));
+      r2 = 0.09f + 0.91f * sigmoidf_(y[6]);
+    }
+    const f3 wo2 = neg(wi);
+
+    // (c) + (e) at x': M directions about n'
+    f3 lo2 = mk(0.f, 0.f, 0.f);
+    bool ok = true;
+    for (int j = 0; j < M && ok; ++j) {
+      const f3 wj = cosine_direction(n2, m.seed, dir_counter(q, M, 1 + j));
+      const f3 lefr = env_lookup(m.env, m.env_h, m.env_w, wj) * brdf_eval(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+      store_pe_bf16(X, t, wj);
+      ok = run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); });
+      if (!ok) break;
+      epilogue_hidden(D1 + lane_off, bias + BI_IB1, H, t);
+      ok = run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); });
+      if (!ok) break;
+      float z0[1];
+      head_fp32<1, 2>(D2 + lane_off, bias + BI_IB2, bias + BI_IW3, bias + BI_IB3, z0);
+      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoidf_(z0[0]);
+      lo2 = lo2 + lefr * v2;
+    }
+    if (!ok) break;
+    lo2 = lo2 * (kPi / (float)M);
+
+    // Eq. 2 and the primary term of Eq. 1
+    const f3 li = le1 * v + lo2 * (1.0f - v);
+    f3 c = li * fr1;
+    if (!valid) c = mk(0.f, 0.f, 0.f);
+
+    // deterministic segmented reduction of the tile's rows into its pixels
+    const int key = valid ? ps : -1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float ox = __shfl_down_sync(0xffffffffu, c.x, off);
+      const float oy = __shfl_down_sync(0xffffffffu, c.y, off);
+      const float oz = __shfl_down_sync(0xffffffffu, c.z, off);
+      const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+      if (lane + off < 32 && ok2 == key) c = mk(c.x + ox, c.y + oy, c.z + oz);
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    wg_sync(wg);   // fpix reads are done before red (same bytes) is written
+    red[t] = head ? make_float4(c.x, c.y, c.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    wg_sync(wg);
+    if (t < npix) {
+      const int ra = max(0, t * N - off0);
+      const int rb = min(nvalid, (t + 1) * N - off0);
+      f3 sum = mk(0.f, 0.f, 0.f);
+      if (t == 0) {
+        const float4 cs = *carry_s;
+        sum = mk(cs.x, cs.y, cs.z);
+      }
+      for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
+        const float4 h = red[r];
+        sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
+      }
+      const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
+      if (complete) {
+        const float sc = kPi / (float)N;
+        out[p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
+      }
+      if (t == npix - 1) *carry_s = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
+    }
+    wg_sync(wg);
+  }
+
+  // ---- teardown: drain, then free TMEM
+  abort = wg_sync_or(wg, abort);
+  if (abort && t == 0) (void)mbar_wait(bar_a, pending_phase);   // let an MMA still in flight finish
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0 && wg == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+cudaError_t prepare_render_bf16() {
+  return cudaFuncSetAttribute(render_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+}
+
+cudaError_t launch_render_bf16(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset, float4* out,
+                               int num_sms, cudaStream_t s) {
+  const long long want = ((long long)P + kWG - 1) / kWG;
+  const int grid = (int)(want < 2LL * num_sms ? want : 2LL * num_sms);
+  render_bf16_kernel<<<grid, kThreadsB, kSmemAlloc, s>>>(m, gb, P, offset, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

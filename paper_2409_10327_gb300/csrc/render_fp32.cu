@@ -25,7 +25,13 @@ constexpr size_t kSmemBytes = (size_t)(WPACK_FLOATS + kWarps * kWarpFloats) * si
 // element (k, row) of an activation buffer
 __device__ __forceinline__ int aidx(int k, int row) { return k * 32 + (k >> 3) * 4 + row; }
 
-// acc[r][c] += sum_k act(k, 8rg + r) * W[k][8cg + c]
+// Column owned by output slot c (0..7) of lane group cg: slots 0-3 are
+// columns 4cg..4cg+3 and slots 4-7 are 32+4cg..32+4cg+3, so that each of the
+// two float4 weight reads of a k step covers one contiguous 128-byte row span
+// (one shared-memory wavefront).
+__device__ __forceinline__ int ocol(int cg, int c) { return (c < 4 ? 0 : 28) + cg * 4 + c; }
+
+// acc[r][c] += sum_k act(k, 8rg + r) * W[k][ocol(cg, c)]
 template <int K>
 __device__ __forceinline__ void warp_gemm(const float* __restrict__ act, const float* __restrict__ W,
                                           float (&acc)[8][8], int rg, int cg) {
@@ -34,9 +40,9 @@ __device__ __forceinline__ void warp_gemm(const float* __restrict__ act, const f
     const float* ap = act + aidx(k, rg * 8);
     const float4 a0 = *reinterpret_cast<const float4*>(ap);
     const float4 a1 = *reinterpret_cast<const float4*>(ap + 4);
-    const float* wp = W + k * 64 + cg * 8;
+    const float* wp = W + k * 64 + cg * 4;
     const float4 w0 = *reinterpret_cast<const float4*>(wp);
-    const float4 w1 = *reinterpret_cast<const float4*>(wp + 4);
+    const float4 w1 = *reinterpret_cast<const float4*>(wp + 32);
     const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
@@ -58,7 +64,7 @@ __device__ __forceinline__ void store_relu_colbias(float* __restrict__ out, cons
                                                    const float* __restrict__ bias, int rg, int cg) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int col = cg * 8 + c;
+    const int col = ocol(cg, c);
     const float b = bias[col];
     float* o = out + aidx(col, rg * 8);
     *reinterpret_cast<float4*>(o) = make_float4(fmaxf(acc[0][c] + b, 0.f), fmaxf(acc[1][c] + b, 0.f),
@@ -73,7 +79,7 @@ __device__ __forceinline__ void store_relu_tilebias(float* __restrict__ out, con
                                                     const float (&bias)[8][8], int rg, int cg) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int col = cg * 8 + c;
+    const int col = ocol(cg, c);
     float* o = out + aidx(col, rg * 8);
     *reinterpret_cast<float4*>(o) =
         make_float4(fmaxf(acc[0][c] + bias[0][c], 0.f), fmaxf(acc[1][c] + bias[1][c], 0.f),
@@ -224,7 +230,7 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) a2b[r][c] += sw[OFF_IB1 + cg * 8 + c];
+        for (int c = 0; c < 8; ++c) a2b[r][c] += sw[OFF_IB1 + ocol(cg, c)];
       __syncwarp();
       zero(acc);
       warp_gemm<kHidden>(actB, sw + OFF_BW2, acc, rg, cg);

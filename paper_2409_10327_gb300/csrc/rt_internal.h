@@ -35,6 +35,23 @@ constexpr int OFF_BB3 = OFF_BW3 + 64 * 8;        // [8]
 constexpr int WPACK_FLOATS = OFF_BB3 + 8;
 static_assert(OFF_BW1 % 4 == 0 && OFF_BW3 % 4 == 0 && WPACK_FLOATS % 4 == 0, "float4 alignment");
 
+// BF16 weight image for the tensor-core path (bytes).  Each matrix is stored
+// as [N rows = outputs][K = 64 inputs] bf16, K-major, in the 128-byte swizzle
+// of tcgen05 shared-memory descriptors: element (n, k) of a tile lives at
+// (n/8)*1024 + (n%8)*128 + (((2k)/16) ^ (n%8))*16 + (2k)%16.
+// I layer 1 takes [f (32, zero beyond L*F) | PE (27) | 0 (5)].
+constexpr int OFFB_IW1 = 0;        // 64 x 64
+constexpr int OFFB_IW2 = 8192;     // 64 x 64
+constexpr int OFFB_IW3 = 16384;    // 16 x 64 (rows 0..1 used)
+constexpr int OFFB_BW1 = 18432;    // 64 x 64 (k < L*F used)
+constexpr int OFFB_BW2 = 26624;    // 64 x 64
+constexpr int OFFB_BW3 = 34816;    // 16 x 64 (rows 0..6 used)
+constexpr int WBF16_BYTES = 36864;
+
+__host__ __device__ constexpr int swz128(int n, int k) {
+  return (n >> 3) * 1024 + (n & 7) * 128 + ((((2 * k) >> 4) ^ (n & 7)) << 4) + ((2 * k) & 15);
+}
+
 // Hash-grid description passed by value to kernels.
 struct GridDesc {
   int levels;
@@ -50,6 +67,8 @@ struct GridDesc {
 struct ModelDesc {
   GridDesc grid;
   const float* wpack;          // WPACK_FLOATS, device
+  const uint8_t* wbf16;        // WBF16_BYTES, device
+  uint32_t* status;            // device status word (timeouts, bounds)
   const float4* env;           // [env_h][env_w]
   int env_h, env_w;
   int lf;                      // L * F
@@ -74,6 +93,11 @@ cudaError_t launch_sample(const ModelDesc& m, const float4* normal, int P, int l
                           float4* dirs, cudaStream_t s);
 cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int level, long long offset,
                          const float* vis, const float4* lin, float4* out, cudaStream_t s);
+cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s);
+cudaError_t launch_render_bf16(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
+                               float4* out, int num_sms, cudaStream_t s);
+// Status-word codes: (kStatusTimeout | where) after a bounded wait gave up.
+constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                float4* out, int num_sms, cudaStream_t s);
 

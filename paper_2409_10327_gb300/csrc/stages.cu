@@ -243,7 +243,11 @@ cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int l
 }
 
 cudaError_t prepare_render_fp32();
+cudaError_t prepare_render_bf16();
 
-cudaError_t prepare_kernels() { return prepare_render_fp32(); }
+cudaError_t prepare_kernels() {
+  cudaError_t e = prepare_render_fp32();
+  return e != cudaSuccess ? e : prepare_render_bf16();
+}
 
 }  // namespace rtk

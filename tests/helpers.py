@@ -59,6 +59,35 @@ def fp32_parity(got: np.ndarray, ref: np.ndarray, sens: np.ndarray):
     return frame <= FP32_FRAME_TOL and not over.any(), stats
 
 
+# BF16 criterion.  The spec bar is PSNR >= 45 dB against the FP64
+# oracle (peak = max of the oracle image), applied to frames shaped like the
+# paper's (N >= 32, M = 8).  With bf16 weights and activations the depth t,
+# and so x', carries ~2^-8 relative error, which moves the finest hash levels
+# by up to a cell, and the rounded weights bias every sample the same way; on
+# degenerate shapes (N = 4, M = 1) single samples dominate a pixel and the
+# exact result itself moves by tens of percent under such perturbations.  So
+# every BF16 comparison also bounds each pixel by 2e-2 |ref| plus 16 times
+# the oracle's response to bf16-sized (unit roundoff 2^-8) perturbations of
+# x', the sphere points, the MLP activations and weights, and FP16-sized ones
+# of the table (render.float32_sensitivity with mlp=True).
+BF16_PSNR_MIN = 45.0
+BF16_PIXEL_TOL = 2e-2
+BF16_SENS_FACTOR = 16.0
+BF16_JITTER = 2.0 ** -8
+
+
+def bf16_parity(got: np.ndarray, ref: np.ndarray, sens: np.ndarray):
+    """(per-pixel bound holds, stats) for the BF16 criterion above."""
+    err = np.abs(got - ref)
+    peak = float(np.abs(ref).max())
+    bound = BF16_PIXEL_TOL * np.maximum(np.abs(ref), 1e-6 * peak) + BF16_SENS_FACTOR * sens
+    stats = {"psnr_db": psnr(got, ref), "max_abs": float(err.max()),
+             "frame_rel_l1": float(err.sum() / max(np.abs(ref).sum(), 1e-300)),
+             "median_rel": float(np.median(err / np.maximum(np.abs(ref), 1e-6 * peak))),
+             "pixels_over_bound": int((err > bound).any(-1).sum()), "pixels": int(ref.shape[0])}
+    return stats["pixels_over_bound"] == 0, stats
+
+
 def psnr(got: np.ndarray, ref: np.ndarray) -> float:
     peak = float(np.abs(ref).max())
     mse = float(((got - ref) ** 2).mean())

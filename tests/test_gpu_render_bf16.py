@@ -1,0 +1,109 @@
+"""BF16 tensor-core render (FP16 table, BF16 MLP operands, FP32 accumulation) against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+from oracle import render as orender
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+PSNR_MIN = helpers.BF16_PSNR_MIN   # dB against the FP64 oracle, peak = max of the oracle image
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_10327_gb300 import build
+    build.build()
+    from paper_2409_10327_gb300 import binding
+    return binding
+
+
+def _render(cfg, sc, gb, offset=0, **ov):
+    r = helpers.renderer_for(cfg, sc, **ov)
+    out = r.render_frame(helpers.to_cuda(gb), pixel_offset=offset)
+    torch.cuda.synchronize()
+    assert r.check() == 0
+    return out.cpu().numpy()
+
+
+def _bf16_check(cfg, sc, gb, out, offset=0, rows=None, psnr_min=PSNR_MIN, **modes):
+    prm = helpers.oracle_params(sc)
+    opt = helpers.oracle_options(cfg, **modes)
+    ref = orender.render(gb, prm, opt, pixel_offset=offset, rows=rows)
+    sens = orender.float32_sensitivity(gb, prm, opt, pixel_offset=offset, rows=rows, rel=helpers.BF16_JITTER,
+                                       draws=4, mlp=True)
+    got = out[:, :3] if rows is None else out[rows, :3]
+    ok, stats = helpers.bf16_parity(got, ref, sens)
+    assert ok, stats
+    if psnr_min is not None:
+        assert stats["psnr_db"] >= psnr_min, stats
+    return stats
+
+
+def _report(got, ref):
+    psnr = helpers.psnr(got, ref)
+    err = np.abs(got - ref)
+    return {"psnr_db": psnr, "max_abs": float(err.max()), "frame_rel_l1": float(err.sum() / np.abs(ref).sum()),
+            "median_rel": float(np.median(err / np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())))}
+
+
+@pytest.mark.parametrize("mode", [{}, {"force_vis": 0.0}])
+def test_bf16_tiny_frame_psnr(lib, mode):
+    cfg = scenegen.CONFIGS["tiny64"]
+    cfg = type(cfg)(**{**cfg.__dict__, "precision": "bf16"})
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    out = _render(cfg, sc, gb, **mode)
+    assert np.all(out[:, 3] == 0)
+    stats = _bf16_check(cfg, sc, gb, out, **mode)
+    assert stats["frame_rel_l1"] < 5e-2, stats   # gross-error guard; bf16 n' under sharp lobes gives a few %
+
+
+def test_bf16_white_furnace(lib):
+    cfg = helpers.small_cfg(n_dirs=64, precision="bf16")
+    sc, gb = helpers.scene_arrays(cfg, 1)
+    sc.env[..., :3] = 1.0
+    out = _render(cfg, sc, gb, force_vis=1.0, brdf_mode=1)
+    np.testing.assert_allclose(out[:, :3], gb["albedo_rough"][:, :3], rtol=2e-6)
+
+
+@pytest.mark.parametrize("n_dirs,m_dirs,levels,log2_T,P", [(40, 3, 5, 12, 37), (4, 1, 1, 10, 45), (96, 8, 16, 19, 19),
+                                                          (256, 2, 16, 19, 3), (33, 16, 3, 9, 64)])
+def test_bf16_ragged_shapes(lib, n_dirs, m_dirs, levels, log2_T, P):
+    cfg = helpers.small_cfg(n_dirs=n_dirs, m_dirs=m_dirs, levels=levels, log2_T=log2_T,
+                            max_res=256 if levels > 1 else 16, precision="bf16")
+    sc, gb = helpers.scene_arrays(cfg, 3, bias=0.2, n_pixels=P)
+    out = _render(cfg, sc, gb, offset=1000)
+    # PSNR is the bar for paper-shaped frames only; every shape gets the per-pixel bound
+    _bf16_check(cfg, sc, gb, out, offset=1000, psnr_min=PSNR_MIN if n_dirs >= 32 and m_dirs >= 8 else None)
+
+
+def test_bf16_sharded_frame_is_bit_identical(lib):
+    cfg = helpers.small_cfg(precision="bf16")
+    sc, gb = helpers.scene_arrays(cfg, 5, n_pixels=300)
+    r = helpers.renderer_for(cfg, sc)
+    dgb = helpers.to_cuda(gb)
+    whole = r.render_frame(dgb).cpu().numpy()
+    parts = [r.render_frame({k: v[lo:hi].contiguous() for k, v in dgb.items()}, pixel_offset=lo).cpu().numpy()
+             for lo, hi in [(0, 77), (77, 78), (78, 300)]]
+    np.testing.assert_array_equal(np.concatenate(parts), whole)
+
+
+def test_bf16_small_n_is_rejected(lib):
+    cfg = helpers.small_cfg(n_dirs=2, precision="bf16")
+    sc, gb = helpers.scene_arrays(cfg, 0, n_pixels=8)
+    r = helpers.renderer_for(cfg, sc)
+    with pytest.raises(lib.RtError) as e:
+        r.render_frame(helpers.to_cuda(gb))
+    assert e.value.status == lib.RT_ERR_UNSUPPORTED
+
+
+def test_bf16_full_size_frame_sampled(lib):
+    # the 800x800, N=128, M=8, L=16, T=2^19 BF16 workload as bench.py launches it
+    cfg = scenegen.CONFIGS["frame800_bf16"]
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    out = _render(cfg, sc, gb)
+    assert np.isfinite(out).all()
+    rows = scenegen.subset_permutation(cfg.n_pixels, 256, seed=0)
+    _bf16_check(cfg, sc, gb, out, rows=rows)
