@@ -268,7 +268,8 @@ def run_ours(args, cfg):
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": args.steps, "clocks": clk,
-            "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms)}}
+            "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
+                          "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
     if world > 1:
         dist.barrier()

@@ -138,8 +138,10 @@ rt_status rt_destroy(rt_ctx* ctx);
 /* Bind the model: table [L][T][F] (float for RT_FP32, IEEE half for RT_BF16;
  * kept by reference), B and I blobs (float, layout of rt_param_count; copied
  * and repacked on `stream` into the context) and env [env_h][env_w][4] float
- * (rgb + ignored lane; kept by reference).  Call again after the weights
- * change. */
+ * (rgb + ignored lane; kept by reference).  The table must be 8-byte
+ * aligned.  Call again after the weights change.  Synchronises `stream`: the
+ * FP32 biases and output layers are copied to the host once here, because
+ * the BF16 kernel takes them as launch parameters. */
 rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, const float* irt_w,
                         const float* env, void* stream);
 

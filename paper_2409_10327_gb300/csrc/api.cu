@@ -20,6 +20,7 @@ struct rt_ctx {
   uint32_t* status;    // device status word
   const void* table;
   const float* env;
+  HeadParams head;     // host copy of the FP32 biases / output layers (BF16 kernel parameter)
   bool ready;
 };
 
@@ -228,16 +229,36 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
                         void* stream) {
   if (ctx == nullptr || table == nullptr || brdf_w == nullptr || irt_w == nullptr || env == nullptr)
     return RT_ERR_INVALID_ARG;
-  const uintptr_t ta = ctx->cfg.precision == RT_BF16 ? 4 : 8;
+  const uintptr_t ta = 8;   // the BF16 kernel reads pairs of FP16 entries as one 8-byte load
   if (!aligned(table, ta) || !aligned(brdf_w, 4) || !aligned(irt_w, 4) || !aligned(env, 16))
     return RT_ERR_INVALID_ARG;
   ctx->table = table;
   ctx->env = env;
   const int lf = ctx->cfg.levels * ctx->cfg.feat_dim;
-  rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, (cudaStream_t)stream));
-  if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, (cudaStream_t)stream));
-  if (st == RT_OK) ctx->ready = true;
-  return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, s));
+  if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, s));
+  if (st != RT_OK) return st;
+  // host copy of the biases and output layers for the BF16 kernel's parameters
+  static thread_local float host[WPACK_FLOATS];
+  if (cudaMemcpyAsync(host, ctx->wpack, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RT_ERR_CUDA;
+  HeadParams& h = ctx->head;
+  for (int i = 0; i < 64; ++i) {
+    h.ib1[i] = host[OFF_IB1 + i];
+    h.ib2[i] = host[OFF_IB2 + i];
+    h.bb1[i] = host[OFF_BB1 + i];
+    h.bb2[i] = host[OFF_BB2 + i];
+    h.iw3[i][0] = host[OFF_IW3 + 2 * i];
+    h.iw3[i][1] = host[OFF_IW3 + 2 * i + 1];
+    for (int o = 0; o < 8; ++o) h.bw3[i][o] = host[OFF_BW3 + 8 * i + o];
+  }
+  h.ib3[0] = host[OFF_IB3];
+  h.ib3[1] = host[OFF_IB3 + 1];
+  for (int o = 0; o < 8; ++o) h.bb3[o] = host[OFF_BB3 + o];
+  ctx->ready = true;
+  return RT_OK;
 }
 
 rt_status rt_check(rt_ctx* ctx, uint32_t* word, void* stream) {
@@ -324,8 +345,8 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
     return cuda_status(launch_render_fp32(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
                                           ctx->num_sms, (cudaStream_t)stream));
   if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;   // the BF16 tile holds at most 33 pixels
-  return cuda_status(launch_render_bf16(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
-                                        ctx->num_sms, (cudaStream_t)stream));
+  return cuda_status(launch_render_bf16(m, ctx->head, *gb, (int)P, pixel_offset,
+                                        reinterpret_cast<float4*>(radiance), ctx->num_sms, (cudaStream_t)stream));
 }
 
 rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* d_radiance,

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "device_common.cuh"
+#include "fast_math.cuh"
 
 namespace rtk {
 
@@ -79,12 +80,7 @@ constexpr int WG_FPIX = 32768;               // primary features [34][32] bf16; 
 constexpr int WG_MISC = WG_FPIX + 2560;      // mbarrier (8), carry (16)
 constexpr int WG_BYTES = 35840;
 constexpr int SM_WG = WBF16_BYTES;
-constexpr int SM_BIAS = SM_WG + kWG * WG_BYTES;          // FP32 biases
-// FP32 biases, then the FP32 output layers (I: W3 [64][2], B: W3 [64][8]) that
-// the epilogues evaluate on the CUDA cores from the FP32 layer-2 accumulator
-constexpr int BI_IB1 = 0, BI_IB2 = 64, BI_IB3 = 128, BI_BB1 = 132, BI_BB2 = 196, BI_BB3 = 260;
-constexpr int BI_IW3 = 268, BI_BW3 = BI_IW3 + 128, BI_N = BI_BW3 + 512;
-constexpr int SM_TMEMSLOT = SM_BIAS + BI_N * 4;
+constexpr int SM_TMEMSLOT = SM_WG + kWG * WG_BYTES;
 constexpr int SM_BYTES = SM_TMEMSLOT + 16;
 constexpr size_t kSmemAlloc = SM_BYTES + 1024;
 static_assert(WG_MISC + 64 <= WG_BYTES, "warpgroup block overflow");
@@ -239,14 +235,17 @@ __device__ __forceinline__ void head_fp32(uint32_t taddr, const float* b2, const
   }
 }
 
-// f' = H(x') as 16 packed bf16 pairs (zero beyond L levels).  The gathers of
-// kEncBatch levels (8 loads each) are issued before any of them is consumed,
-// so a thread waits on the L2 16 / kEncBatch times per point instead of 16.
+
+// f' = H(x') as 16 packed bf16 pairs (zero beyond L levels), from an FP16
+// table.  The two x-neighbour corners of a cell share one 8-byte load when
+// their rows form an aligned pair (rows r and r ^ 1: a hashed level with even
+// i, or a dense level with an even row), which removes about a quarter of
+// the gathers.  The loads of kEncBatch levels are issued before any is used.
 constexpr int kEncBatch = 2;
 __device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint32_t (&fq)[16]) {
 #pragma unroll
   for (int l0 = 0; l0 < kMaxLevels; l0 += kEncBatch) {
-    uint32_t v[kEncBatch][8];   // raw half2 table entries (the BF16 path always reads an FP16 table)
+    uint32_t v[kEncBatch][8];
     float w[kEncBatch][3];
 #pragma unroll
     for (int b = 0; b < kEncBatch; ++b) {
@@ -257,12 +256,16 @@ __device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint3
         grid_cell(x.x, res, ix, w[b][0]);
         grid_cell(x.y, res, iy, w[b][1]);
         grid_cell(x.z, res, iz, w[b][2]);
-        const size_t base = (size_t)l << g.log2T;
-        const uint32_t* tab = reinterpret_cast<const uint32_t*>(g.table) + base;
+        const uint32_t* tab = reinterpret_cast<const uint32_t*>(g.table) + ((size_t)l << g.log2T);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          v[b][c] = __ldg(tab + corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res, g.dense[l],
-                                           g.mask));
+        for (int yz = 0; yz < 4; ++yz) {
+          const uint32_t r0 = corner_row(ix, iy + (yz & 1), iz + (yz >> 1), res, g.dense[l], g.mask);
+          const uint32_t r1 = corner_row(ix + 1, iy + (yz & 1), iz + (yz >> 1), res, g.dense[l], g.mask);
+          const uint2 pr = __ldg(reinterpret_cast<const uint2*>(tab + (r0 & ~1u)));
+          const bool odd = r0 & 1u;
+          v[b][2 * yz] = odd ? pr.y : pr.x;
+          v[b][2 * yz + 1] = ((r0 ^ r1) == 1u) ? (odd ? pr.x : pr.y) : __ldg(tab + r1);
+        }
       }
     }
 #pragma unroll
@@ -272,8 +275,10 @@ __device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint3
       if (l < g.levels) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const float wt = ((c & 1) ? w[b][0] : 1.0f - w[b][0]) * ((c & 2) ? w[b][1] : 1.0f - w[b][1]) *
-                           ((c & 4) ? w[b][2] : 1.0f - w[b][2]);
+          // v[b][2*yz + dx] holds corner (dx, yz & 1, yz >> 1)
+          const int dx = c & 1, yz = c >> 1;
+          const float wt = (dx ? w[b][0] : 1.0f - w[b][0]) * ((yz & 1) ? w[b][1] : 1.0f - w[b][1]) *
+                           ((yz & 2) ? w[b][2] : 1.0f - w[b][2]);
           const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[b][c]));
           f0 = fmaf(wt, e.x, f0);
           f1 = fmaf(wt, e.y, f1);
@@ -287,7 +292,7 @@ __device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint3
 // PE(w) as bf16 into chunks 4..7 of the A tile row (27 values, then zeros)
 __device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
   float pe[32];
-  positional_encoding(w, [&](int k, float v) { pe[k] = v; });
+  positional_encoding_fast(w, [&](int k, float v) { pe[k] = v; });
 #pragma unroll
   for (int k = kPE; k < 32; ++k) pe[k] = 0.0f;
 #pragma unroll
@@ -297,7 +302,8 @@ __device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
 }
 
 __global__ void __launch_bounds__(kThreadsB, 2)
-render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, float4* __restrict__ out) {
+render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P, long long pixel_offset,
+                   float4* __restrict__ out) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
@@ -310,24 +316,11 @@ render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
   float4* red = reinterpret_cast<float4*>(wgb + WG_FPIX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WG_MISC);
   float4* carry_s = reinterpret_cast<float4*>(wgb + WG_MISC + 16);
-  float* bias = reinterpret_cast<float*>(sm + SM_BIAS);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SM_TMEMSLOT);
 
   // ---- CTA set-up: weights and biases into shared memory, TMEM, barriers
   for (int i = tid; i < WBF16_BYTES / 16; i += kThreadsB)
     reinterpret_cast<uint4*>(Wsm)[i] = __ldg(reinterpret_cast<const uint4*>(m.wbf16) + i);
-  for (int i = tid; i < BI_N; i += kThreadsB) {
-    float v = 0.0f;
-    if (i < 64) v = m.wpack[OFF_IB1 + i];
-    else if (i < 128) v = m.wpack[OFF_IB2 + i - 64];
-    else if (i < 130) v = m.wpack[OFF_IB3 + i - 128];
-    else if (i >= BI_BB1 && i < BI_BB1 + 64) v = m.wpack[OFF_BB1 + i - BI_BB1];
-    else if (i >= BI_BB2 && i < BI_BB2 + 64) v = m.wpack[OFF_BB2 + i - BI_BB2];
-    else if (i >= BI_BB3 && i < BI_BB3 + 7) v = m.wpack[OFF_BB3 + i - BI_BB3];
-    else if (i >= BI_IW3 && i < BI_IW3 + 128) v = m.wpack[OFF_IW3 + i - BI_IW3];
-    else if (i >= BI_BW3) v = m.wpack[OFF_BW3 + i - BI_BW3];
-    bias[i] = v;
-  }
   if (t == 0) {
     mbar_init(smem_u32(bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -435,11 +428,11 @@ render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
     const f3 wo = xyz(view4[p]);
     const float4 ar = ar4[p];
     const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
-    const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+    const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
     // Eq. 1 factors of the primary direction, fetched before the MMAs so the
     // env-map loads overlap them
-    const f3 le1 = env_lookup(m.env, m.env_h, m.env_w, wi);
-    const f3 fr1 = brdf_eval(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+    const f3 le1 = env_lookup_fast(m.env, m.env_h, m.env_w, wi);
+    const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
     {
       const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
 #pragma unroll
@@ -452,14 +445,14 @@ render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
 
     // (c) I(f, w_i)
     if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); })) break;
-    epilogue_hidden(D1 + lane_off, bias + BI_IB1, H, t);
+    epilogue_hidden(D1 + lane_off, hp.ib1, H, t);
     if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); })) break;
     float v, tdep;
     {
       float z[2];
-      head_fp32<2, 2>(D2 + lane_off, bias + BI_IB2, bias + BI_IW3, bias + BI_IB3, z);
-      v = m.force_vis >= 0.f ? m.force_vis : sigmoidf_(z[0]);
-      tdep = depth_from_logit(z[1], m.near_t, m.far_t);
+      head_fp32<2, 2>(D2 + lane_off, hp.ib2, &hp.iw3[0][0], hp.ib3, z);
+      v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
+      tdep = depth_fast(z[1], m.near_t, m.far_t);
     }
 
     // (d) bounce: x' = x + t w_i; f' = H(x') into chunks 0..3 of the A tile
@@ -473,17 +466,17 @@ render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
 
     // (b) B(f')
     if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_BW1, 2, kIdescN64); })) break;
-    epilogue_hidden(D1 + lane_off, bias + BI_BB1, H, t);
+    epilogue_hidden(D1 + lane_off, hp.bb1, H, t);
     if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_BW2, 4, kIdescN64); })) break;
     f3 n2, a2;
     float r2;
     {
       float y[7];
-      head_fp32<7, 8>(D2 + lane_off, bias + BI_BB2, bias + BI_BW3, bias + BI_BB3, y);
+      head_fp32<7, 8>(D2 + lane_off, hp.bb2, &hp.bw3[0][0], hp.bb3, y);
       const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
       n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
-      a2 = mk(sigmoidf_(y[3]), sigmoidf_(y[4]), sigmoidf_(y[5]));
-      r2 = 0.09f + 0.91f * sigmoidf_(y[6]);
+      a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
+      r2 = 0.09f + 0.91f * sigmoid_fast(y[6]);
     }
     const f3 wo2 = neg(wi);
 
@@ -491,17 +484,17 @@ render_bf16_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
     f3 lo2 = mk(0.f, 0.f, 0.f);
     bool ok = true;
     for (int j = 0; j < M && ok; ++j) {
-      const f3 wj = cosine_direction(n2, m.seed, dir_counter(q, M, 1 + j));
-      const f3 lefr = env_lookup(m.env, m.env_h, m.env_w, wj) * brdf_eval(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+      const f3 wj = cosine_direction_fast(n2, m.seed, dir_counter(q, M, 1 + j));
+      const f3 lefr = env_lookup_fast(m.env, m.env_h, m.env_w, wj) * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
       store_pe_bf16(X, t, wj);
       ok = run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); });
       if (!ok) break;
-      epilogue_hidden(D1 + lane_off, bias + BI_IB1, H, t);
+      epilogue_hidden(D1 + lane_off, hp.ib1, H, t);
       ok = run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); });
       if (!ok) break;
       float z0[1];
-      head_fp32<1, 2>(D2 + lane_off, bias + BI_IB2, bias + BI_IW3, bias + BI_IB3, z0);
-      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoidf_(z0[0]);
+      head_fp32<1, 2>(D2 + lane_off, hp.ib2, &hp.iw3[0][0], hp.ib3, z0);
+      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(z0[0]);
       lo2 = lo2 + lefr * v2;
     }
     if (!ok) break;
@@ -565,11 +558,11 @@ cudaError_t prepare_render_bf16() {
   return cudaFuncSetAttribute(render_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
 }
 
-cudaError_t launch_render_bf16(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset, float4* out,
-                               int num_sms, cudaStream_t s) {
+cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
+                               long long offset, float4* out, int num_sms, cudaStream_t s) {
   const long long want = ((long long)P + kWG - 1) / kWG;
   const int grid = (int)(want < 2LL * num_sms ? want : 2LL * num_sms);
-  render_bf16_kernel<<<grid, kThreadsB, kSmemAlloc, s>>>(m, gb, P, offset, out);
+  render_bf16_kernel<<<grid, kThreadsB, kSmemAlloc, s>>>(m, hp, gb, P, offset, out);
   return cudaGetLastError();
 }
 

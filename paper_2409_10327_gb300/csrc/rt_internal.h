@@ -80,6 +80,16 @@ struct ModelDesc {
   uint64_t seed;
 };
 
+// FP32 biases and output layers of both MLPs, passed to the BF16 kernel by
+// value as a kernel parameter (constant bank) so that its epilogues read them
+// without shared-memory traffic.  Filled on the host by rt_set_params.
+struct HeadParams {
+  float ib1[64], ib2[64], ib3[2];
+  float bb1[64], bb2[64], bb3[8];
+  float iw3[64][2];
+  float bw3[64][8];
+};
+
 // Launch helpers implemented in the .cu files.
 // One-time per-device kernel attributes (large dynamic shared memory); called by rt_create.
 cudaError_t prepare_kernels();
@@ -94,8 +104,8 @@ cudaError_t launch_sample(const ModelDesc& m, const float4* normal, int P, int l
 cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int level, long long offset,
                          const float* vis, const float4* lin, float4* out, cudaStream_t s);
 cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s);
-cudaError_t launch_render_bf16(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
-                               float4* out, int num_sms, cudaStream_t s);
+cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
+                               long long offset, float4* out, int num_sms, cudaStream_t s);
 // Status-word codes: (kStatusTimeout | where) after a bounded wait gave up.
 constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
