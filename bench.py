@@ -4,7 +4,9 @@
 
 One step renders one 800x800 frame (N = 128 directions per pixel, M = 8 per
 secondary point, L = 16 levels, T = 2^19, resolutions 16..2048, 64x128 env)
-through the C ABI, i.e. one launch of the fused kernel.  Four seeded scenes
+through the C ABI, i.e. one launch of the fused kernel; the headline is the
+BF16 tensor-core path (FP16 table) and the FP32 path of the same workload is
+timed in the same run under "compare".  Four seeded scenes
 (tables, MLPs, env maps and G-buffers, about 420 MB in FP32) are rotated
 step by step, so every step starts with its inputs out of the 129 MB L2.
 Under torchrun each rank renders its own scenes (weak scaling, no data-path
@@ -37,7 +39,7 @@ UNIT = "samples/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 FFMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-L2_NOTE = "4 scenes rotated, one per step (~105 MB each in FP32, 420 MB total > 129 MB L2)"
+L2_NOTE = "4 scenes rotated, one per step (73 MB each in BF16, 105 MB in FP32; 290-420 MB in total > 129 MB L2)"
 
 
 def algorithmic_flop_per_sample(cfg) -> int:
@@ -151,16 +153,9 @@ def run_reference(args, cfg):
     print(json.dumps(line))
 
 
-def run_ours(args, cfg):
+def _setup(cfg, rank, n_scenes=4):
     import torch
-    import torch.distributed as dist
-    rank, local, world = dist_info()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     from paper_2409_10327_gb300 import binding
-
-    n_scenes = 4
     renderers, gbs = [], []
     for s in range(n_scenes):
         seed = rank * n_scenes + s
@@ -173,38 +168,82 @@ def run_ours(args, cfg):
                      torch.from_numpy(sc.env).cuda())
         renderers.append(r)
         gbs.append({k: torch.from_numpy(v).cuda() for k, v in scenegen.make_gbuffer(cfg.n_pixels, seed).items()})
-    out = torch.empty(cfg.n_pixels, 4, device="cuda")
+    return renderers, gbs
+
+
+def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
+    """Kernel-time the fused render over `steps` frames rotating the scenes; returns (total ms, per-launch ms)."""
+    import torch
     stream = torch.cuda.current_stream()
+    n = len(renderers)
+    for w in range(warmup):
+        renderers[w % n].render_frame(gbs[w % n], out=out)
+    barrier()
+    if clocks is not None:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        renderers[k % n].render_frame(gbs[k % n], out=out)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks is not None else None
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev], clk
+
+
+def _roofline(cfg, launch_ms, peaks):
+    flop = algorithmic_flop_per_sample(cfg) * cfg.samples
+    avg_s = sum(launch_ms) / len(launch_ms) / 1e3
+    if cfg.precision == "fp32":
+        roof = {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained")
+        roof = {"bound": "tensor", "achieved": flop / avg_s / 1e12, "peak": pk if pk else 1700.0, "unit": "TFLOP/s",
+                "peak_source": "of measured (bf16_tflops_sustained)" if pk else "of fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["algorithmic_per_launch"] = flop
+    roof["kernel_ms"] = avg_s * 1e3
+    gather_bytes = cfg.samples * cfg.levels * 8 * (4 if cfg.precision == "bf16" else 8)
+    hbm = peaks.get("hbm_gbs")
+    roof["gather"] = {"algorithmic_bytes_per_launch": gather_bytes, "achieved_GBps": gather_bytes / avg_s / 1e9,
+                      "hbm_peak_GBps": hbm, "frac_of_hbm": (gather_bytes / avg_s / 1e9 / hbm) if hbm else None,
+                      "note": "table is L2-resident; the scattered-gather limit is L1TEX wavefronts"}
+    return roof
+
+
+def run_ours(args, cfg):
+    import dataclasses
+    import torch
+    import torch.distributed as dist
+    rank, local, world = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for w in range(args.warmup):
-        renderers[w % n_scenes].render_frame(gbs[w % n_scenes], out=out)
-    barrier()
+    def max_over_ranks(x):
+        if world > 1:
+            tt = torch.tensor([x], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            return float(tt.item())
+        return x
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    t0.record(stream)
-    for k in range(args.steps):
-        ev[k][0].record(stream)
-        renderers[k % n_scenes].render_frame(gbs[k % n_scenes], out=out)
-        ev[k][1].record(stream)
-    t1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    renderers, gbs = _setup(cfg, rank)
+    out = torch.empty(cfg.n_pixels, 4, device="cuda")
+    total_ms, launch_ms, clk = _time_frames(renderers, gbs, out, args.steps, args.warmup, barrier,
+                                            ClockSampler(local))
+    total_ms = max_over_ranks(total_ms)
     ms_step = total_ms / args.steps
     value = world * cfg.samples * args.steps / (total_ms / 1e3)
 
@@ -212,23 +251,39 @@ def run_ours(args, cfg):
     host_gb = [{k: v.cpu().pin_memory() for k, v in g.items()} for g in gbs]
     host_out = torch.empty(cfg.n_pixels, 4).pin_memory()
     staging = {k: torch.empty_like(v) for k, v in gbs[0].items()}
+    n = len(renderers)
     for w in range(max(1, args.warmup)):
-        renderers[w % n_scenes].render_frame_host(host_gb[w % n_scenes], host_out, staging, out)
+        renderers[w % n].render_frame_host(host_gb[w % n], host_out, staging, out)
     barrier()
+    stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        renderers[k % n_scenes].render_frame_host(host_gb[k % n_scenes], host_out, staging, out)
+        renderers[k % n].render_frame_host(host_gb[k % n], host_out, staging, out)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     h2d = sum(v.numel() * v.element_size() for v in host_gb[0].values())
     d2h = host_out.numel() * host_out.element_size()
+    for r in renderers:
+        r.close()
+    del renderers, gbs, host_gb, staging
+
+    # the other precision of the same workload, for the BF16-vs-FP32 comparison
+    compare = None
+    if not args.no_compare:
+        other = dataclasses.replace(cfg, precision="fp32" if cfg.precision == "bf16" else "bf16")
+        rs, gs = _setup(other, rank)
+        steps = max(3, args.steps // 4)
+        o_total, o_launch, _ = _time_frames(rs, gs, out, steps, args.warmup, barrier)
+        o_total = max_over_ranks(o_total)
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        compare = {"precision": other.precision, "value": world * other.samples * steps / (o_total / 1e3),
+                   "unit": UNIT, "ms_per_frame": o_total / steps, "steps": steps,
+                   "roofline": _roofline(other, o_launch, peaks)}
+        for r in rs:
+            r.close()
 
     if rank != 0:
         if world > 1:
@@ -236,23 +291,7 @@ def run_ours(args, cfg):
             dist.destroy_process_group()
         return
 
-    flop = algorithmic_flop_per_sample(cfg) * cfg.samples
-    avg_launch_s = sum(launch_ms) / len(launch_ms) / 1e3
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        peaks = json.load(open(PEAKS_FILE))
-    if cfg.precision == "fp32":
-        roof = {"bound": "alu", "achieved": flop / avg_launch_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal)"}
-    else:
-        pk = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": flop / avg_launch_s / 1e12, "peak": pk, "unit": "TFLOP/s",
-                "peak_source": "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["algorithmic_per_launch"] = flop
-    roof["kernel_ms"] = avg_launch_s * 1e3
-
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, done, el, cores = cpu_oracle_rate(cfg, args.cpu_seconds)
@@ -263,11 +302,11 @@ def run_ours(args, cfg):
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if cfg.precision == "fp32" else "bf16",
             "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": n_scenes},
-            "roofline": roof, "cpu_baseline": cpu,
+            "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": 4},
+            "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": args.steps, "clocks": clk,
+            "gpu_launches": args.steps, "clocks": clk, "compare": compare,
             "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
                           "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
@@ -281,7 +320,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other precision's comparison timing")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="frame800")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
