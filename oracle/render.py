@@ -260,7 +260,7 @@ def distill_gradient(gb, rows, student: Params, target: torch.Tensor, opt: Optio
     g_table = student.table.grad.clone()
     g_brdf = torch.cat([t.grad.reshape(-1) for wb in student.brdf for t in wb])
     g_irt = torch.cat([t.grad.reshape(-1) for wb in student.irt for t in wb])
-    return float(loss), g_table, g_brdf, g_irt
+    return float(loss.detach()), g_table, g_brdf, g_irt
 
 
 def upstream_gradient(student_rad: np.ndarray, target_rad: np.ndarray) -> np.ndarray:

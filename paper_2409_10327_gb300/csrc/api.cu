@@ -353,11 +353,14 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
                       float* g_table, float* g_brdf, float* g_irt, void* stream) {
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
-  if (P < 0 || P > kMaxP || pixel_offset < 0 || !check_gbuffer(gb) || !check_plane(d_radiance) ||
-      g_table == nullptr || g_brdf == nullptr || g_irt == nullptr)
+  if (P < 0 || P > kMaxP || pixel_offset < 0) return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (!check_gbuffer(gb) || !check_plane(d_radiance) || g_table == nullptr || !aligned(g_table, 8) ||
+      g_brdf == nullptr || !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))
     return RT_ERR_INVALID_ARG;
-  (void)stream;
-  return RT_ERR_UNSUPPORTED;
+  return cuda_status(launch_backward_fp32(model_desc(ctx), *gb, (int)P, pixel_offset,
+                                          reinterpret_cast<const float4*>(d_radiance), g_table, g_brdf, g_irt,
+                                          ctx->num_sms, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -1,0 +1,583 @@
+// Hand-written adjoint of the fused renderer (rt_backward).
+//
+// The loss is any function of the radiance; the caller supplies dLoss/dL per
+// pixel.  Gradients flow to the hash table (both encodes) and to every weight
+// and bias of B and I.  Sampled directions are constants of the estimator.
+// Activations are recomputed, never stored in global memory.
+//
+// Work unit: as in the FP32 forward, one warp owns one primary point and its
+// directions 32 at a time (lane = direction i).  For every chunk the warp
+//   1. recomputes I(f, w_i), the bounce, f' = H(x') and B(f'),
+//   2. runs each secondary I(f', w'_j) forward and immediately backward
+//      (dv'_j and dfr2_j only need dLo2 = (1 - v) dL_i, which is known),
+//      collecting dLoss/df' and dLoss/d(a', r', n'),
+//   3. back-propagates B (recomputed), then the encode at x': table
+//      gradients by float2 atomics and dLoss/dx' through the trilinear
+//      weights (zero on a clamped axis),
+//   4. turns dx' into dt = dx' . w_i and dz1 through min(softplus, 1), adds
+//      dz0 from dv = dL_i . (Lenv(w_i) - L'_o,i), and back-propagates the
+//      primary I (recomputed) into its weights and into dLoss/df.
+// After the pixel's last chunk the primary encode scatters dLoss/df into the
+// table.  Weight gradients of each chunk are small warp GEMMs added to a
+// per-CTA shared-memory accumulator (padded rows, shared atomics), which the
+// CTA adds to the caller's gradient blobs once at the end.
+#include "warp_gemm.cuh"
+
+namespace rtk {
+
+namespace {
+
+constexpr int kBW = 3;                     // warps per CTA
+constexpr int kBT = 32 * kBW;
+// gradient accumulator layout in shared memory (floats; rows padded to K + 1)
+constexpr int LD_I1 = 60;                  // >= L*F + 27 + 1
+constexpr int LD_B1 = 33;                  // >= L*F + 1
+constexpr int LD_2 = 65;
+constexpr int GI_W1 = 0, GI_B1 = GI_W1 + 64 * LD_I1, GI_W2 = GI_B1 + 64, GI_B2 = GI_W2 + 64 * LD_2;
+constexpr int GI_W3 = GI_B2 + 64, GI_B3 = GI_W3 + 2 * LD_2;
+constexpr int GB_W1 = GI_B3 + 4, GB_B1 = GB_W1 + 64 * LD_B1, GB_W2 = GB_B1 + 64, GB_B2 = GB_W2 + 64 * LD_2;
+constexpr int GB_W3 = GB_B2 + 64, GB_B3 = GB_W3 + 7 * LD_2;
+constexpr int G_FLOATS = (GB_B3 + 8 + 3) / 4 * 4;
+// per-warp buffers (floats)
+constexpr int WB_F2 = 0;                                   // f' of the chunk's rows  [32 cols]
+constexpr int WB_PE = WB_F2 + kActStride32;                 // PE of the current direction [32 cols]
+constexpr int WB_H1 = WB_PE + kActStride32;                 // layer-1 activations [64 cols]
+constexpr int WB_H2 = WB_H1 + kActStride;                   // layer-2 activations, then dZ1 [64 cols]
+constexpr int WB_DZ2 = WB_H2 + kActStride;                  // dZ2 [64 cols]
+constexpr int WB_DZ = WB_DZ2 + kActStride;                  // output gradients [8][32]
+constexpr int WB_FP = WB_DZ + 8 * 32;                       // primary feature f [32]
+constexpr int WB_AP = WB_FP + 32;                           // primary b1 + W1f f [64]
+constexpr int WB_DFP = WB_AP + 64;                          // dLoss/df of the pixel [32]
+constexpr int WB_FLOATS = WB_DFP + 32;
+constexpr size_t kBSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kBW * WB_FLOATS) * sizeof(float);
+static_assert(LD_I1 >= 32 + 27 + 1 && LD_B1 >= 33, "gradient rows");
+static_assert(WB_F2 % 4 == 0 && WB_PE % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 && WB_DZ2 % 4 == 0 &&
+                  WB_DZ % 4 == 0 && WB_FLOATS % 4 == 0 && G_FLOATS % 4 == 0,
+              "float4 alignment");
+
+// s = D F Vis of the simplified Disney model and its derivatives with respect
+// to the roughness r and the normal n (w_i, w_o fixed).  The n-derivative is
+// the textbook one (n.h, n.w_i, n.w_o as independent inputs); the component
+// along n is irrelevant because the decoder's normal is normalised.
+__device__ __forceinline__ float spec_with_grad(float rough, f3 n, f3 wi, f3 wo, float f0, float& ds_dr, f3& ds_dn) {
+  const float alpha = rough * rough;
+  const float a2 = alpha * alpha;
+  const float ndl = dot(n, wi), ndv = dot(n, wo);
+  const float nol = fmaxf(ndl, 0.0f), nov = fmaxf(ndv, 1e-4f);
+  const f3 hv = wi + wo;
+  const float hl2 = dot(hv, hv);
+  f3 h = mk(0.f, 0.f, 0.f);
+  float ndh = 0.0f, voh = 0.0f, q = 1.0f;
+  if (hl2 > 1e-20f) {
+    const float inv = rsqrtf(hl2);
+    h = hv * inv;
+    ndh = dot(n, h);
+    voh = 0.5f * hl2 * inv;
+    if (ndh > 0.0f) {
+      const f3 c = cross(n, h);
+      q = dot(c, c) + ndh * ndh * a2;     // = (n.h)^2 (a2 - 1) + 1 on the unit sphere
+    }
+  }
+  const float noh = fmaxf(ndh, 0.0f);
+  const float D = a2 / (kPi * q * q);
+  const float om = 1.0f - voh;
+  const float om2 = om * om;
+  const float F = f0 + (1.0f - f0) * (om2 * om2 * om);
+  const float A = sqrtf(nov * nov * (1.0f - a2) + a2);
+  const float B = sqrtf(nol * nol * (1.0f - a2) + a2);
+  const float den = nol * A + nov * B;
+  const float vis = 0.5f / den;
+  const float dD_da2 = 1.0f / (kPi * q * q) - 2.0f * a2 * noh * noh / (kPi * q * q * q);
+  const float dD_dnoh = -4.0f * a2 * noh * (a2 - 1.0f) / (kPi * q * q * q);
+  const float dvis_dden = -0.5f / (den * den);
+  const float dden_da2 = nol * (1.0f - nov * nov) / (2.0f * A) + nov * (1.0f - nol * nol) / (2.0f * B);
+  const float dden_dnol = A + nov * nol * (1.0f - a2) / B;
+  const float dden_dnov = nol * nov * (1.0f - a2) / A + B;
+  const float ds_da2 = F * (dD_da2 * vis + D * dvis_dden * dden_da2);
+  ds_dr = ds_da2 * 4.0f * rough * rough * rough;
+  const float g_nol = ndl > 0.0f ? F * D * dvis_dden * dden_dnol : 0.0f;
+  const float g_nov = ndv > 1e-4f ? F * D * dvis_dden * dden_dnov : 0.0f;
+  const float g_noh = ndh > 0.0f ? F * vis * dD_dnoh : 0.0f;
+  ds_dn = wi * g_nol + wo * g_nov + h * g_noh;
+  return D * F * vis;
+}
+
+// ---- warp-level pieces of an MLP backward -----------------------------------
+
+// DZ2(c, row) = (sum_o dz[o][row] W3[c][o]) * [H2(c, row) > 0]   (thread per row)
+template <int NOUT, int LDW>
+__device__ __forceinline__ void bwd_head(const float* H2, const float* dz, const float* W3, float* DZ2, int lane) {
+  float g[NOUT];
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) g[o] = dz[o * 32 + lane];
+#pragma unroll 8
+  for (int c = 0; c < 64; ++c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) s = fmaf(g[o], W3[c * LDW + o], s);
+    DZ2[aidx(c, lane)] = H2[aidx(c, lane)] > 0.0f ? s : 0.0f;
+  }
+}
+
+// dW3[o][k] += sum_rows H2(k, row) dz[o][row]; db3[o] += sum_rows dz[o][row]
+template <int NOUT>
+__device__ __forceinline__ void bwd_w3(const float* H2, const float* dz, float* gW3, float* gb3, int lane) {
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int k = 2 * lane + kk;
+    float acc[NOUT];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) acc[o] = 0.0f;
+    for (int r = 0; r < 32; ++r) {
+      const float h = H2[aidx(k, r)];
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) acc[o] = fmaf(h, dz[o * 32 + r], acc[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) atomicAdd(gW3 + o * LD_2 + k, acc[o]);
+  }
+  if (lane < NOUT) {
+    float s = 0.0f;
+    for (int r = 0; r < 32; ++r) s += dz[lane * 32 + r];
+    atomicAdd(gb3 + lane, s);
+  }
+}
+
+// dW[c][koff + k] += sum_rows A(k, row) D(c, row) for k < K, c in {2 lane, 2 lane + 1};
+// if gb != nullptr also db[c] += sum_rows D(c, row)
+__device__ __forceinline__ void bwd_weights(const float* A, int K, const float* D, float* gW, int ld, int koff,
+                                            float* gb, int lane) {
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc) {
+    const int c = 2 * lane + cc;
+    float d[32];
+#pragma unroll
+    for (int r = 0; r < 32; r += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(D + aidx(c, r));
+      d[r] = v.x;
+      d[r + 1] = v.y;
+      d[r + 2] = v.z;
+      d[r + 3] = v.w;
+    }
+    if (gb != nullptr) {
+      float s = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 32; ++r) s += d[r];
+      atomicAdd(gb + c, s);
+    }
+    for (int k = 0; k < K; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 32; r += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(A + aidx(k, r));
+        s = fmaf(a.x, d[r], s);
+        s = fmaf(a.y, d[r + 1], s);
+        s = fmaf(a.z, d[r + 2], s);
+        s = fmaf(a.w, d[r + 3], s);
+      }
+      atomicAdd(gW + c * ld + koff + k, s);
+    }
+  }
+}
+
+// OUT(k, row) = (sum_c D(c, row) W[k][c]) * [MASK(k, row) > 0] for k < 64 (thread per row);
+// W is a [64][64] shared matrix stored [k][c]
+__device__ __forceinline__ void bwd_hidden(const float* D, const float* W, const float* MASK, float* OUT, int lane) {
+  float d[64];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) d[c] = D[aidx(c, lane)];
+  for (int k = 0; k < 64; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 64; c += 4) {
+      const float4 w = *reinterpret_cast<const float4*>(W + k * 64 + c);
+      s = fmaf(d[c], w.x, s);
+      s = fmaf(d[c + 1], w.y, s);
+      s = fmaf(d[c + 2], w.z, s);
+      s = fmaf(d[c + 3], w.w, s);
+    }
+    OUT[aidx(k, lane)] = MASK[aidx(k, lane)] > 0.0f ? s : 0.0f;
+  }
+}
+
+// din[k] += sum_c D(c, row) W[k][c] for k < K (thread per row)
+__device__ __forceinline__ void bwd_input(const float* D, const float* W, int K, float (&din)[32], int lane) {
+  float d[64];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) d[c] = D[aidx(c, lane)];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < K) {
+      float s = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 64; c += 4) {
+        const float4 w = *reinterpret_cast<const float4*>(W + k * 64 + c);
+        s = fmaf(d[c], w.x, s);
+        s = fmaf(d[c + 1], w.y, s);
+        s = fmaf(d[c + 2], w.z, s);
+        s = fmaf(d[c + 3], w.w, s);
+      }
+      din[k] += s;
+    }
+  }
+}
+
+// trilinear encode adjoint at point x for one level: table gradient scatter
+// and (optionally) dLoss/dx
+__device__ __forceinline__ void encode_level_bwd(const GridDesc& g, int l, f3 x, float df0, float df1,
+                                                 float* __restrict__ g_table, f3* dx) {
+  const int res = g.res[l];
+  uint32_t ix, iy, iz;
+  float wx, wy, wz;
+  grid_cell(x.x, res, ix, wx);
+  grid_cell(x.y, res, iy, wy);
+  grid_cell(x.z, res, iz, wz);
+  const size_t base = (size_t)l << g.log2T;
+  const int dense = g.dense[l];
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+    const uint32_t row = corner_row(ix + ox, iy + oy, iz + oz, res, dense, g.mask);
+    const float ax = ox ? wx : 1.0f - wx, ay = oy ? wy : 1.0f - wy, az = oz ? wz : 1.0f - wz;
+    const float w = ax * ay * az;
+    atomicAdd(reinterpret_cast<float2*>(g_table) + base + row, make_float2(w * df0, w * df1));
+    if (dx != nullptr) {
+      const float2 e = table_entry(g, base + row);
+      const float de = e.x * df0 + e.y * df1;
+      gx += de * (ox ? 1.0f : -1.0f) * ay * az;
+      gy += de * (oy ? 1.0f : -1.0f) * ax * az;
+      gz += de * (oz ? 1.0f : -1.0f) * ax * ay;
+    }
+  }
+  if (dx != nullptr) {
+    // dg/dx = N_l / 2 inside the box, 0 on a clamped axis
+    const float s = 0.5f * (float)res;
+    const float ux = x.x * 0.5f + 0.5f, uy = x.y * 0.5f + 0.5f, uz = x.z * 0.5f + 0.5f;
+    dx->x += (ux >= 0.0f && ux <= 1.0f) ? gx * s : 0.0f;
+    dx->y += (uy >= 0.0f && uy <= 1.0f) ? gy * s : 0.0f;
+    dx->z += (uz >= 0.0f && uz <= 1.0f) ? gz * s : 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(kBT, 1)
+backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, const float4* __restrict__ dL,
+                     float* __restrict__ g_table, float* __restrict__ g_brdf, float* __restrict__ g_irt) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  float* sg = sw + WPACK_FLOATS;
+  for (int i = threadIdx.x; i < WPACK_FLOATS / 4; i += kBT)
+    smem4[i] = __ldg(reinterpret_cast<const float4*>(m.wpack) + i);
+  for (int i = threadIdx.x; i < G_FLOATS; i += kBT) sg[i] = 0.0f;
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 3, cg = lane & 7;
+  float* wb = sg + G_FLOATS + warp * WB_FLOATS;
+  float* F2 = wb + WB_F2;
+  float* PEb = wb + WB_PE;
+  float* H1 = wb + WB_H1;
+  float* H2 = wb + WB_H2;
+  float* DZ2 = wb + WB_DZ2;
+  float* DZ = wb + WB_DZ;
+  float* fP = wb + WB_FP;
+  float* aP = wb + WB_AP;
+  float* dfP = wb + WB_DFP;
+  const int N = m.N, M = m.M, lf = m.lf, lfp = m.lfp;
+  const bool disney = !m.lambert;
+  const float4* pos4 = reinterpret_cast<const float4*>(gb.pos);
+  const float4* nrm4 = reinterpret_cast<const float4*>(gb.normal);
+  const float4* view4 = reinterpret_cast<const float4*>(gb.view);
+  const float4* ar4 = reinterpret_cast<const float4*>(gb.albedo_rough);
+
+  for (int pix = blockIdx.x * kBW + warp; pix < P; pix += gridDim.x * kBW) {
+    const f3 x = xyz(pos4[pix]);
+    const f3 n = xyz(nrm4[pix]);
+    const f3 wo = xyz(view4[pix]);
+    const float4 ar = ar4[pix];
+    const f3 G = xyz(dL[pix]);
+
+    // primary feature and I's layer-1 bias for the point (as in the forward)
+    {
+      const int l = lane >> 1;
+      float2 part = make_float2(0.f, 0.f);
+      if (l < m.grid.levels) {
+        const float2 f = encode_level(m.grid, l, x);
+        part = (lane & 1) ? make_float2(0.f, 0.f) : f;
+      }
+      if ((lane & 1) == 0) {
+        fP[lane] = part.x;
+        fP[lane + 1] = part.y;
+      }
+      dfP[lane] = 0.0f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      float acc = sw[OFF_IB1 + c];
+      for (int k = 0; k < lfp; ++k) acc = fmaf(fP[k], sw[OFF_IW1F + k * 64 + c], acc);
+      aP[c] = acc;
+    }
+    __syncwarp();
+
+    for (int i0 = 0; i0 < N; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < N;
+      const uint64_t q = (uint64_t)(pixel_offset + pix) * (uint64_t)N + (uint64_t)i;
+      const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+      float acc[8][8];
+
+      // ---- forward of I(f, w_i)
+      store_pe(PEb, wi, lane);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kPEPad>(PEb, sw + OFF_IW1P, acc, rg, cg);
+      store_relu_colbias(H1, acc, aP, rg, cg);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(H1, sw + OFF_IW2, acc, rg, cg);
+      store_relu_colbias(H2, acc, sw + OFF_IB2, rg, cg);
+      __syncwarp();
+      const float2 z = irt_head(H2, sw, lane);
+      const float v = m.force_vis >= 0.f ? m.force_vis : sigmoidf_(z.x);
+      const float sp = softplusf_(z.y);
+      const float t = m.near_t + (m.far_t - m.near_t) * fminf(sp, 1.0f);
+      const f3 x2 = x + wi * t;
+
+      // ---- f' = H(x') into F2, then B(f')
+      __syncwarp();
+      for (int l = 0; l < m.grid.levels; ++l) {
+        const float2 f = encode_level(m.grid, l, x2);
+        F2[aidx(2 * l, lane)] = f.x;
+        F2[aidx(2 * l + 1, lane)] = f.y;
+      }
+      for (int k = lf; k < 32; ++k) F2[aidx(k, lane)] = 0.0f;
+      __syncwarp();
+      zero(acc);
+      warp_gemm_k(F2, sw + OFF_BW1, acc, lfp, rg, cg);
+      store_relu_colbias(H1, acc, sw + OFF_BB1, rg, cg);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(H1, sw + OFF_BW2, acc, rg, cg);
+      store_relu_colbias(H2, acc, sw + OFF_BB2, rg, cg);
+      __syncwarp();
+      float y[7];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) y[o] = sw[OFF_BB3 + o];
+      for (int k = 0; k < kHidden; ++k) {
+        const float hk = H2[aidx(k, lane)];
+#pragma unroll
+        for (int o = 0; o < 7; ++o) y[o] = fmaf(hk, sw[OFF_BW3 + 8 * k + o], y[o]);
+      }
+      const float nlen = sqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+      const f3 n2 = mk(y[0] / nlen, y[1] / nlen, y[2] / nlen);
+      const f3 a2 = mk(sigmoidf_(y[3]), sigmoidf_(y[4]), sigmoidf_(y[5]));
+      const float s6 = sigmoidf_(y[6]);
+      const float r2 = 0.09f + 0.91f * s6;
+      const f3 wo2 = neg(wi);
+
+      // ---- primary shading factors and the incoming-radiance gradient
+      const f3 e1 = env_lookup(m.env, m.env_h, m.env_w, wi);
+      const f3 fr1 = brdf_eval(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      const float sN = kPi / (float)N, sM = kPi / (float)M;
+      const f3 dli = valid ? (G * fr1) * sN : mk(0.f, 0.f, 0.f);
+      const f3 dlo2 = dli * (1.0f - v);
+
+      // ---- secondary directions: forward and backward of I(f', w'_j)
+      float dF2[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) dF2[k] = 0.0f;
+      f3 lo2 = mk(0.f, 0.f, 0.f), da2 = mk(0.f, 0.f, 0.f), dn2 = mk(0.f, 0.f, 0.f);
+      float dr2 = 0.0f;
+      for (int j = 0; j < M; ++j) {
+        const f3 wj = cosine_direction(n2, m.seed, dir_counter(q, M, 1 + j));
+        __syncwarp();
+        store_pe(PEb, wj, lane);
+        __syncwarp();
+        zero(acc);
+        warp_gemm_k(F2, sw + OFF_IW1F, acc, lfp, rg, cg);
+        warp_gemm<kPEPad>(PEb, sw + OFF_IW1P, acc, rg, cg);
+        store_relu_colbias(H1, acc, sw + OFF_IB1, rg, cg);
+        __syncwarp();
+        zero(acc);
+        warp_gemm<kHidden>(H1, sw + OFF_IW2, acc, rg, cg);
+        store_relu_colbias(H2, acc, sw + OFF_IB2, rg, cg);
+        __syncwarp();
+        const float z0 = irt_head(H2, sw, lane).x;
+        const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoidf_(z0);
+        const f3 le = env_lookup(m.env, m.env_h, m.env_w, wj);
+        float ds_dr = 0.0f;
+        f3 ds_dn = mk(0.f, 0.f, 0.f);
+        const float s = disney ? spec_with_grad(r2, n2, wj, wo2, m.f0, ds_dr, ds_dn) : 0.0f;
+        const f3 fr2 = mk(a2.x * kInvPi + s, a2.y * kInvPi + s, a2.z * kInvPi + s);
+        const f3 ef = le * fr2;
+        lo2 = lo2 + ef * v2;
+        // Eq. 1 at x': dLo2 -> dv'_j, d fr2
+        const float dv2 = sM * dot(dlo2, ef);
+        const f3 dfr = (dlo2 * le) * (sM * v2);
+        da2 = da2 + dfr * kInvPi;
+        if (disney) {
+          const float dsum = dfr.x + dfr.y + dfr.z;
+          dr2 += dsum * ds_dr;
+          dn2 = dn2 + ds_dn * dsum;
+        }
+        const float dz0 = m.force_vis2 >= 0.f ? 0.0f : dv2 * v2 * (1.0f - v2);
+        DZ[lane] = dz0;
+        __syncwarp();
+        // I backward: head, W3, W2, hidden, W1 (f' and PE parts), input f'
+        bwd_head<1, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
+        bwd_w3<1>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
+        __syncwarp();
+        bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+        bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);          // dZ1 into H2
+        __syncwarp();
+        bwd_weights(F2, lf, H2, sg + GI_W1, LD_I1, 0, sg + GI_B1, lane);
+        bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, nullptr, lane);
+        bwd_input(H2, sw + OFF_IW1F, lf, dF2, lane);
+      }
+      lo2 = lo2 * sM;
+      const float dv = dot(dli, e1 - lo2);
+
+      // ---- B backward (forward recomputed)
+      float dy[7];
+      {
+        const float dnn = dot(n2, dn2);
+        dy[0] = (dn2.x - n2.x * dnn) / nlen;
+        dy[1] = (dn2.y - n2.y * dnn) / nlen;
+        dy[2] = (dn2.z - n2.z * dnn) / nlen;
+        dy[3] = da2.x * a2.x * (1.0f - a2.x);
+        dy[4] = da2.y * a2.y * (1.0f - a2.y);
+        dy[5] = da2.z * a2.z * (1.0f - a2.z);
+        dy[6] = dr2 * 0.91f * s6 * (1.0f - s6);
+      }
+      __syncwarp();
+      zero(acc);
+      warp_gemm_k(F2, sw + OFF_BW1, acc, lfp, rg, cg);
+      store_relu_colbias(H1, acc, sw + OFF_BB1, rg, cg);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(H1, sw + OFF_BW2, acc, rg, cg);
+      store_relu_colbias(H2, acc, sw + OFF_BB2, rg, cg);
+#pragma unroll
+      for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
+      __syncwarp();
+      bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, DZ2, lane);
+      bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
+      __syncwarp();
+      bwd_weights(H1, 64, DZ2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+      bwd_hidden(DZ2, sw + OFF_BW2, H1, H2, lane);
+      __syncwarp();
+      bwd_weights(F2, lf, H2, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+      bwd_input(H2, sw + OFF_BW1, lf, dF2, lane);
+
+      // ---- encode adjoint at x': table gradients and dLoss/dx'
+      f3 dx2 = mk(0.f, 0.f, 0.f);
+      if (valid) {
+        for (int l = 0; l < m.grid.levels; ++l) {
+          float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (k == l) {
+              d0 = dF2[2 * k];
+              d1 = dF2[2 * k + 1];
+            }
+          encode_level_bwd(m.grid, l, x2, d0, d1, g_table, &dx2);
+        }
+      }
+      const float dt = dot(dx2, wi);
+      const float dz1 = (sp <= 1.0f) ? dt * (m.far_t - m.near_t) * sigmoidf_(z.y) : 0.0f;
+      const float dz0p = (m.force_vis >= 0.f || !valid) ? 0.0f : dv * v * (1.0f - v);
+
+      // ---- primary I backward (forward recomputed)
+      __syncwarp();
+      store_pe(PEb, wi, lane);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kPEPad>(PEb, sw + OFF_IW1P, acc, rg, cg);
+      store_relu_colbias(H1, acc, aP, rg, cg);
+      __syncwarp();
+      zero(acc);
+      warp_gemm<kHidden>(H1, sw + OFF_IW2, acc, rg, cg);
+      store_relu_colbias(H2, acc, sw + OFF_IB2, rg, cg);
+      DZ[lane] = dz0p;
+      DZ[32 + lane] = valid ? dz1 : 0.0f;
+      __syncwarp();
+      bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
+      bwd_w3<2>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
+      __syncwarp();
+      bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+      bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);
+      __syncwarp();
+      bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
+      // the f part of layer 1 is shared by the chunk's rows: dW1f[c][k] += f[k] colsum(dZ1)[c]
+      // and dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        float cs = 0.0f;
+        for (int r = 0; r < 32; ++r) cs += H2[aidx(c, r)];
+        DZ2[c] = cs;   // reuse as scratch: column sums of dZ1
+      }
+      __syncwarp();
+      for (int k = 0; k < lf; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = lane + 32 * h;
+          atomicAdd(sg + GI_W1 + c * LD_I1 + k, fP[k] * DZ2[c]);
+        }
+      }
+      if (lane < lf) {
+        float s = 0.0f;
+        for (int c = 0; c < 64; ++c) s = fmaf(DZ2[c], sw[OFF_IW1F + lane * 64 + c], s);
+        dfP[lane] += s;
+      }
+      __syncwarp();
+    }
+
+    // ---- primary encode adjoint: table gradients at x
+    {
+      const int l = lane >> 1;
+      if ((lane & 1) == 0 && l < m.grid.levels) encode_level_bwd(m.grid, l, x, dfP[lane], dfP[lane + 1], g_table, nullptr);
+    }
+    __syncwarp();
+  }
+
+  // ---- flush the CTA's weight gradients into the caller's blobs (canonical layouts)
+  __syncthreads();
+  const int lfv = m.lf, in_i = lfv + kPE;
+  const int iW1 = 0, iB1 = 64 * in_i, iW2 = iB1 + 64, iB2 = iW2 + 4096, iW3 = iB2 + 64, iB3 = iW3 + 128;
+  const int bW1 = 0, bB1 = 64 * lfv, bW2 = bB1 + 64, bB2 = bW2 + 4096, bW3 = bB2 + 64, bB3 = bW3 + 448;
+  for (int e = threadIdx.x; e < 64 * in_i; e += kBT) atomicAdd(g_irt + iW1 + e, sg[GI_W1 + (e / in_i) * LD_I1 + e % in_i]);
+  for (int e = threadIdx.x; e < 64; e += kBT) {
+    atomicAdd(g_irt + iB1 + e, sg[GI_B1 + e]);
+    atomicAdd(g_irt + iB2 + e, sg[GI_B2 + e]);
+    atomicAdd(g_brdf + bB1 + e, sg[GB_B1 + e]);
+    atomicAdd(g_brdf + bB2 + e, sg[GB_B2 + e]);
+  }
+  for (int e = threadIdx.x; e < 4096; e += kBT) {
+    atomicAdd(g_irt + iW2 + e, sg[GI_W2 + (e / 64) * LD_2 + e % 64]);
+    atomicAdd(g_brdf + bW2 + e, sg[GB_W2 + (e / 64) * LD_2 + e % 64]);
+  }
+  for (int e = threadIdx.x; e < 128; e += kBT) atomicAdd(g_irt + iW3 + e, sg[GI_W3 + (e / 64) * LD_2 + e % 64]);
+  for (int e = threadIdx.x; e < 2; e += kBT) atomicAdd(g_irt + iB3 + e, sg[GI_B3 + e]);
+  for (int e = threadIdx.x; e < 64 * lfv; e += kBT) atomicAdd(g_brdf + bW1 + e, sg[GB_W1 + (e / lfv) * LD_B1 + e % lfv]);
+  for (int e = threadIdx.x; e < 448; e += kBT) atomicAdd(g_brdf + bW3 + e, sg[GB_W3 + (e / 64) * LD_2 + e % 64]);
+  for (int e = threadIdx.x; e < 7; e += kBT) atomicAdd(g_brdf + bB3 + e, sg[GB_B3 + e]);
+}
+
+}  // namespace
+
+cudaError_t prepare_backward_fp32() {
+  return cudaFuncSetAttribute(backward_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
+}
+
+cudaError_t launch_backward_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset, const float4* dL,
+                                 float* g_table, float* g_brdf, float* g_irt, int num_sms, cudaStream_t s) {
+  const int need = (P + kBW - 1) / kBW;
+  const int grid = need < num_sms ? need : num_sms;
+  backward_fp32_kernel<<<grid, kBT, kBSmem, s>>>(m, gb, P, offset, dL, g_table, g_brdf, g_irt);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

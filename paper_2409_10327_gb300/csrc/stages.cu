@@ -244,10 +244,13 @@ cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int l
 
 cudaError_t prepare_render_fp32();
 cudaError_t prepare_render_bf16();
+cudaError_t prepare_backward_fp32();
 
 cudaError_t prepare_kernels() {
   cudaError_t e = prepare_render_fp32();
-  return e != cudaSuccess ? e : prepare_render_bf16();
+  if (e == cudaSuccess) e = prepare_render_bf16();
+  if (e == cudaSuccess) e = prepare_backward_fp32();
+  return e;
 }
 
 }  // namespace rtk
