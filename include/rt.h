@@ -206,6 +206,34 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
                       const float* d_radiance, float* g_table, float* g_brdf, float* g_irt,
                       void* stream);
 
+/* ---- rendering without any device allocation ---------------------------- */
+
+/* rt_render_frame for callers that cannot allocate device memory: a host
+ * whose memory manager owns every device allocation (pools or arenas that
+ * forbid direct cudaMalloc), or a frame loop with a fixed device-memory
+ * budget where an allocation, or the synchronisation a free implies, is not
+ * allowed.  The paper has no counterpart: this is a deployment variant of the
+ * fused FP32 kernel.  It needs no context: cfg describes the renderer and
+ * the model arrays are passed directly, in the layouts of rt_set_params
+ * (float table [L][T][F], 8-byte aligned; FP32 B and I blobs; env
+ * [env_h][env_w][4]).  The packed weight image that rt_create would allocate
+ * lives instead in one file-scope device array of 15,244 floats (61 KB), which
+ * every GPU that loads the library keeps until the process exits; it is
+ * rewritten in full by every call, so it needs no clearing.
+ *  - precision must be RT_FP32 (else RT_ERR_UNSUPPORTED); L*F must fit the
+ *    array's 32 feature rows (else RT_ERR_INVALID_ARG; every valid config does);
+ *  - the first call on a device finds the array's device address
+ *    (cudaGetSymbolAddress) and sets the kernel's shared-memory limit, with
+ *    that device current; make that first call before any stream capture;
+ *  - all calls on a device share the array: calls whose work overlaps on the
+ *    GPU (different streams, or different models in flight) race; serialise
+ *    them on one stream;
+ *  - no cudaMalloc, cudaFree or allocating library routine is called.
+ * Results equal rt_render_frame's for the same inputs. */
+rt_status rt_render_frame_static(const rt_config* cfg, const void* table, const float* brdf_w, const float* irt_w,
+                                 const float* env, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
+                                 float* radiance, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ RT_DISNEY, RT_LAMBERT = 0, 1
 EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level_resolution",
            "rt_level_is_dense", "rt_param_count", "rt_workspace_bytes", "rt_create", "rt_destroy",
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
-           "rt_render_frame", "rt_backward"]
+           "rt_render_frame", "rt_backward", "rt_render_frame_static"]
 
 
 class RtConfig(ctypes.Structure):
@@ -74,6 +74,7 @@ def _load() -> ctypes.CDLL:
         "rt_shade": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I32, I64, P, P, P, P]),
         "rt_render_frame": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, P]),
         "rt_backward": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, P, P, P, P]),
+        "rt_render_frame_static": (I32, [cfgp, P, P, P, P, ctypes.POINTER(RtGbuffer), I64, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
