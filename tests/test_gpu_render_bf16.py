@@ -106,4 +106,22 @@ def test_bf16_full_size_frame_sampled(lib):
     out = _render(cfg, sc, gb)
     assert np.isfinite(out).all()
     rows = scenegen.subset_permutation(cfg.n_pixels, 256, seed=0)
-    _bf16_check(cfg, sc, gb, out, rows=rows)
+    stats = _bf16_check(cfg, sc, gb, out, rows=rows, psnr_min=None)
+    # PSNR is defined with the peak of the whole FP64 oracle image; the sample's
+    # MSE estimates the frame's.  The peak comes from tests/golden (written by
+    # make_frame_stats.py from the oracle alone).
+    peak = _golden_stat("frame800_seed0_stats.txt", "peak")
+    prm = helpers.oracle_params(sc)
+    ref = orender.render(gb, prm, helpers.oracle_options(cfg), rows=rows)
+    mse = float(((out[rows, :3] - ref) ** 2).mean())
+    frame_psnr = 10.0 * np.log10(peak * peak / mse)
+    assert frame_psnr >= PSNR_MIN, (frame_psnr, stats)
+
+
+def _golden_stat(name, key):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    for line in open(path):
+        if line.startswith(key + " "):
+            return float(line.split()[1])
+    raise KeyError(key)
