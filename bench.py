@@ -315,6 +315,65 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Batched serving: V views x E lights at 1920x1080 (N=256, L=16, T=2^20, BF16), one CUDA-graph launch."""
+    import torch
+    rank, local, world = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2409_10327_gb300 import binding, serve
+    cfg = scenegen.CONFIGS["serve1080"]
+    V, E = args.views, args.lights
+    sc = scenegen.make_scene(cfg, 0)
+    r = binding.Renderer(binding.make_config(cfg))
+    r.set_params(torch.from_numpy(sc.table).cuda().half(), torch.from_numpy(sc.brdf_blob).cuda(),
+                 torch.from_numpy(sc.irt_blob).cuda(), torch.from_numpy(sc.env).cuda())
+    gbs = [{k: torch.from_numpy(v).cuda() for k, v in scenegen.make_gbuffer(cfg.n_pixels, rank * V + v).items()}
+           for v in range(V)]
+    envs = torch.from_numpy(np.stack([scenegen.make_env(cfg.env_h, cfg.env_w, 100 + e) for e in range(E)])).cuda()
+    srv = serve.BatchedServer(r, gbs, envs)
+    tuned_ms = srv.tune()
+    shape = r.launch_shape()
+    srv.capture()
+    for _ in range(args.warmup):
+        srv.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    lats = []
+    t0.record()
+    for _ in range(args.steps):
+        srv.replay()
+        t1.record()
+        torch.cuda.synchronize()
+        lats += srv.view_latencies_ms()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    frames = V * E * args.steps
+    samples = cfg.samples * V * args.steps          # secondary samples of the geometry passes
+    lat = np.array(lats)
+    if rank != 0:
+        return
+    line = {"metric": "batched serving: secondary samples/s and frame latency (16 views x 8 env maps, 1920x1080)",
+            "value": samples / (total_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"serve1080: {V} views x {E} env maps, 1920x1080, N=256, M=8, L=16, T=2^20, bf16",
+                       "graph": "one CUDA graph per batch (one rt_render_frame_multi per view)",
+                       "launch_shape": {"lights_per_launch": shape[0], "warpgroups": shape[1], "tuned_ms": tuned_ms}},
+            "frames_per_s": frames / (total_ms / 1e3), "lit_samples_per_s": samples * E / (total_ms / 1e3),
+            "view_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                "views": int(lat.size)},
+            "frame_latency_ms_amortised": {"p50": float(np.percentile(lat, 50)) / E,
+                                           "p99": float(np.percentile(lat, 99)) / E},
+            "gpu_launches": args.steps * V * max(1, E // shape[0]), "clocks": clk}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,6 +386,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["frame", "serve"], default="frame")
+    ap.add_argument("--views", type=int, default=16)
+    ap.add_argument("--lights", type=int, default=8)
     ap.add_argument("--pixels", type=int, default=0,
                     help="render only the first P pixel rows of each frame (a smaller case for profilers)")
     args = ap.parse_args()
@@ -336,6 +398,8 @@ def main():
         cfg = dataclasses.replace(cfg, name=cfg.name + f"[{args.pixels} px]", width=args.pixels, height=1)
     if args.impl == "reference":
         run_reference(args, cfg)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args, cfg)
 

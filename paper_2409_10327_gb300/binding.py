@@ -26,7 +26,8 @@ RT_DISNEY, RT_LAMBERT = 0, 1
 EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level_resolution",
            "rt_level_is_dense", "rt_param_count", "rt_workspace_bytes", "rt_create", "rt_destroy",
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
-           "rt_render_frame", "rt_backward", "rt_render_frame_static"]
+           "rt_render_frame", "rt_backward", "rt_render_frame_static", "rt_render_frame_multi", "rt_tune",
+           "rt_tuned_shape", "rt_set_launch_shape"]
 
 
 class RtConfig(ctypes.Structure):
@@ -75,6 +76,10 @@ def _load() -> ctypes.CDLL:
         "rt_render_frame": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, P]),
         "rt_backward": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, P, P, P, P]),
         "rt_render_frame_static": (I32, [cfgp, P, P, P, P, ctypes.POINTER(RtGbuffer), I64, I64, P, P]),
+        "rt_render_frame_multi": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, I32, P, P]),
+        "rt_tune": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, I32, P, P, ctypes.POINTER(ctypes.c_float)]),
+        "rt_tuned_shape": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "rt_set_launch_shape": (I32, [P, I32, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,6 +232,35 @@ class Renderer:
         _check("rt_render_frame", LIB.rt_render_frame(self.ctx, ctypes.byref(g), P, pixel_offset, _ptr(out),
                                                       _stream()))
         return out
+
+    def render_frame_multi(self, gb: Dict[str, torch.Tensor], envs: torch.Tensor, pixel_offset: int = 0,
+                           out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Radiance [E, P, 4] of the G-buffer under the E maps envs [E, H, W, 4]."""
+        P, E = gb["pos"].shape[0], envs.shape[0]
+        if out is None:
+            out = torch.empty(E, P, 4, device=gb["pos"].device, dtype=torch.float32)
+        g = gbuffer(gb)
+        _check("rt_render_frame_multi", LIB.rt_render_frame_multi(self.ctx, ctypes.byref(g), P, pixel_offset,
+                                                                  _ptr(envs), E, _ptr(out), _stream()))
+        return out
+
+    def tune(self, gb: Dict[str, torch.Tensor], envs: torch.Tensor, pixel_offset: int = 0) -> float:
+        """rt_tune on this workload; returns the best time in ms (-1 for FP32)."""
+        P, E = gb["pos"].shape[0], envs.shape[0]
+        out = torch.empty(E, P, 4, device=gb["pos"].device, dtype=torch.float32)
+        best = ctypes.c_float(0.0)
+        g = gbuffer(gb)
+        _check("rt_tune", LIB.rt_tune(self.ctx, ctypes.byref(g), P, pixel_offset, _ptr(envs), E, _ptr(out),
+                                      _stream(), ctypes.byref(best)))
+        return best.value
+
+    def launch_shape(self):
+        nl, wg = ctypes.c_int32(), ctypes.c_int32()
+        _check("rt_tuned_shape", LIB.rt_tuned_shape(self.ctx, ctypes.byref(nl), ctypes.byref(wg)))
+        return nl.value, wg.value
+
+    def set_launch_shape(self, lights_per_launch: int, warpgroups: int) -> None:
+        _check("rt_set_launch_shape", LIB.rt_set_launch_shape(self.ctx, lights_per_launch, warpgroups))
 
     def render_frame_host(self, gb_host: Dict[str, torch.Tensor], out_host: torch.Tensor,
                           staging: Dict[str, torch.Tensor], out_dev: torch.Tensor, pixel_offset: int = 0) -> None:

@@ -22,6 +22,8 @@ struct rt_ctx {
   const float* env;
   HeadParams head;     // host copy of the FP32 biases / output layers (BF16 kernel parameter)
   bool ready;
+  int tuned_nl;        // lights per launch of the BF16 kernel (rt_tune), default 8
+  int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 2
 };
 
 namespace {
@@ -179,6 +181,8 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
   rt_ctx* ctx = new (std::nothrow) rt_ctx{};
   if (ctx == nullptr) return RT_ERR_OOM;
   ctx->cfg = *cfg;
+  ctx->tuned_nl = 8;
+  ctx->tuned_wg = 2;
   for (int l = 0; l < cfg->levels; ++l) {
     ctx->res[l] = level_res(cfg, l);
     ctx->dense[l] = level_dense(cfg, ctx->res[l]) ? 1 : 0;
@@ -345,8 +349,106 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
     return cuda_status(launch_render_fp32(m, *gb, (int)P, pixel_offset, reinterpret_cast<float4*>(radiance),
                                           ctx->num_sms, (cudaStream_t)stream));
   if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;   // the BF16 tile holds at most 33 pixels
-  return cuda_status(launch_render_bf16(m, ctx->head, *gb, (int)P, pixel_offset,
-                                        reinterpret_cast<float4*>(radiance), ctx->num_sms, (cudaStream_t)stream));
+  return cuda_status(launch_render_bf16_lights(m, ctx->head, *gb, (int)P, pixel_offset, m.env, 1,
+                                               reinterpret_cast<float4*>(radiance), ctx->num_sms, 1, ctx->tuned_wg,
+                                               (cudaStream_t)stream));
+}
+
+rt_status rt_render_frame_multi(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
+                                const float* envs, int32_t E, float* radiance, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || P > kMaxP || pixel_offset < 0 || E < 0 || E > 1024 || P * (int64_t)E > (int64_t)1 << 40)
+    return RT_ERR_INVALID_ARG;
+  if (P == 0 || E == 0) return RT_OK;
+  if (!check_gbuffer(gb) || !check_plane(envs) || !check_plane(radiance)) return RT_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const ModelDesc m = model_desc(ctx);
+  const float4* env4 = reinterpret_cast<const float4*>(envs);
+  float4* out4 = reinterpret_cast<float4*>(radiance);
+  if (ctx->cfg.precision == RT_BF16) {
+    if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;
+    return cuda_status(launch_render_bf16_lights(m, ctx->head, *gb, (int)P, pixel_offset, env4, E, out4,
+                                                 ctx->num_sms, ctx->tuned_nl, ctx->tuned_wg, s));
+  }
+  // FP32: one full pass per light
+  const int64_t hw = (int64_t)ctx->cfg.env_h * ctx->cfg.env_w;
+  for (int e = 0; e < E; ++e) {
+    ModelDesc me = m;
+    me.env = env4 + e * hw;
+    st = cuda_status(launch_render_fp32(me, *gb, (int)P, pixel_offset, out4 + e * P, ctx->num_sms, s));
+    if (st != RT_OK) return st;
+  }
+  return RT_OK;
+}
+
+rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* envs, int32_t E,
+                  float* radiance, void* stream, float* best_ms) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P <= 0 || P > kMaxP || E <= 0 || E > 1024 || pixel_offset < 0 || !check_gbuffer(gb) || !check_plane(envs) ||
+      !check_plane(radiance))
+    return RT_ERR_INVALID_ARG;
+  if (ctx->cfg.precision != RT_BF16) {
+    if (best_ms) *best_ms = -1.0f;
+    return RT_OK;   // the FP32 path has a single launch shape
+  }
+  if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return RT_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RT_ERR_CUDA;
+  }
+  const ModelDesc m = model_desc(ctx);
+  const float4* env4 = reinterpret_cast<const float4*>(envs);
+  float4* out4 = reinterpret_cast<float4*>(radiance);
+  float best = 3.0e38f;
+  int best_nl = ctx->tuned_nl, best_wg = ctx->tuned_wg;
+  st = RT_OK;
+  for (int wg = 1; wg <= 2 && st == RT_OK; ++wg) {
+    for (int nl = 1; nl <= 8 && st == RT_OK; nl *= 2) {
+      if (nl > 1 && nl / 2 >= E) break;   // wider launches than E lights repeat the previous shape
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {   // rep 0 warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess ||
+            launch_render_bf16_lights(m, ctx->head, *gb, (int)P, pixel_offset, env4, E, out4, ctx->num_sms, nl, wg,
+                                      s) != cudaSuccess ||
+            cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          st = RT_ERR_CUDA;
+      }
+      if (st == RT_OK && ms < best) {
+        best = ms;
+        best_nl = nl;
+        best_wg = wg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RT_OK) return st;
+  ctx->tuned_nl = best_nl;
+  ctx->tuned_wg = best_wg;
+  if (best_ms) *best_ms = best;
+  return RT_OK;
+}
+
+rt_status rt_tuned_shape(const rt_ctx* ctx, int32_t* lights_per_launch, int32_t* warpgroups) {
+  if (ctx == nullptr || lights_per_launch == nullptr || warpgroups == nullptr) return RT_ERR_INVALID_ARG;
+  *lights_per_launch = ctx->tuned_nl;
+  *warpgroups = ctx->tuned_wg;
+  return RT_OK;
+}
+
+rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t warpgroups) {
+  if (ctx == nullptr) return RT_ERR_INVALID_ARG;
+  const int nl = lights_per_launch;
+  if (!(nl == 1 || nl == 2 || nl == 4 || nl == 8) || !(warpgroups == 1 || warpgroups == 2)) return RT_ERR_INVALID_ARG;
+  ctx->tuned_nl = nl;
+  ctx->tuned_wg = warpgroups;
+  return RT_OK;
 }
 
 rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* d_radiance,

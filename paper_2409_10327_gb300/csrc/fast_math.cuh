@@ -104,6 +104,44 @@ __device__ __forceinline__ f3 env_lookup_fast(const float4* __restrict__ env, in
             b * (a * e00.z + fs * e01.z) + fq * (a * e10.z + fs * e11.z));
 }
 
+// The same lookup split in two: the texel taps and weights of a direction
+// (the arctangents), computed once, then the fetch from one map, so that a
+// direction can be shaded against several environment maps of one size.
+struct EnvTap {
+  int o00, o01, o10, o11;   // texel offsets (row * W + column)
+  float fs, fq;             // bilinear weights along s and q
+};
+__device__ __forceinline__ EnvTap env_tap_fast(int H, int W, f3 w) {
+  const float phi = atan2_fast(w.y, w.x);
+  const float theta = atan2_fast(sqrtf(w.x * w.x + w.y * w.y), w.z);
+  const float s = (phi + kPi) * ((float)W * (0.5f * kInvPi)) - 0.5f;
+  const float q = theta * ((float)H * kInvPi) - 0.5f;
+  const float s0f = floorf(s), q0f = floorf(q);
+  EnvTap t;
+  t.fs = s - s0f;
+  t.fq = q - q0f;
+  int c0 = (int)s0f;
+  c0 = c0 < 0 ? c0 + W : (c0 >= W ? c0 - W : c0);
+  c0 = min(max(c0, 0), W - 1);
+  const int c1 = (c0 + 1 == W) ? 0 : c0 + 1;
+  const int q0 = (int)q0f;
+  const int r0 = min(max(q0, 0), H - 1);
+  const int r1 = min(max(q0 + 1, 0), H - 1);
+  t.o00 = r0 * W + c0;
+  t.o01 = r0 * W + c1;
+  t.o10 = r1 * W + c0;
+  t.o11 = r1 * W + c1;
+  return t;
+}
+__device__ __forceinline__ f3 env_fetch(const float4* __restrict__ env, const EnvTap& t) {
+  const float4 e00 = __ldg(env + t.o00), e01 = __ldg(env + t.o01);
+  const float4 e10 = __ldg(env + t.o10), e11 = __ldg(env + t.o11);
+  const float a = 1.0f - t.fs, b = 1.0f - t.fq;
+  return mk(b * (a * e00.x + t.fs * e01.x) + t.fq * (a * e10.x + t.fs * e11.x),
+            b * (a * e00.y + t.fs * e01.y) + t.fq * (a * e10.y + t.fs * e11.y),
+            b * (a * e00.z + t.fs * e01.z) + t.fq * (a * e10.z + t.fs * e11.z));
+}
+
 __device__ __forceinline__ f3 brdf_eval_fast(f3 albedo, float rough, f3 n, f3 wi, f3 wo, float f0, int lambert) {
   const f3 d = albedo * kInvPi;
   if (lambert) return d;

@@ -68,23 +68,29 @@ cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t 
 
 namespace {
 
-constexpr int kWG = 2;                       // warpgroups per CTA
-constexpr int kThreadsB = 128 * kWG;
-constexpr int kTmemCols = 256;               // 128 per warpgroup: D1 = [0, 64), D2 = [64, 128)
+// Kernel variants: NL lights per launch (1, 2, 4, 8), WG warpgroups per CTA
+// (1: three CTAs per SM; 2: two CTAs per SM).  Each warpgroup owns 128 TMEM
+// columns: D1 = [0, 64), D2 = [64, 128).
 constexpr int kPixSlots = 34;                // pixels touched by one tile when N >= 4
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int SM_W = 0;
 constexpr int WG_X = 0;                      // A tile [128][64] bf16, swizzled
 constexpr int WG_H = 16384;                  // hidden activations [128][64] bf16, swizzled
 constexpr int WG_FPIX = 32768;               // primary features [34][32] bf16; reused as red[128] float4
-constexpr int WG_MISC = WG_FPIX + 2560;      // mbarrier (8), carry (16)
+constexpr int WG_MISC = WG_FPIX + 2560;      // mbarrier (8), then carry[NL] float4 from +16
 constexpr int WG_BYTES = 35840;
 constexpr int SM_WG = WBF16_BYTES;
-constexpr int SM_TMEMSLOT = SM_WG + kWG * WG_BYTES;
-constexpr int SM_BYTES = SM_TMEMSLOT + 16;
-constexpr size_t kSmemAlloc = SM_BYTES + 1024;
-static_assert(WG_MISC + 64 <= WG_BYTES, "warpgroup block overflow");
+static_assert(WG_MISC + 16 + 8 * 16 <= WG_BYTES, "warpgroup block overflow");
 static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
+
+template <int WG>
+struct Layout {
+  static constexpr int kThreads = 128 * WG;
+  static constexpr int kTmemCols = 128 * WG;
+  static constexpr int kTmemSlot = SM_WG + WG * WG_BYTES;
+  static constexpr size_t kSmem = kTmemSlot + 16 + 1024;
+  static constexpr int kMinBlocks = WG == 1 ? 3 : 2;
+};
 
 constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -301,9 +307,11 @@ __device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
              pack_bf16(pe[8 * c + 4], pe[8 * c + 5]), pack_bf16(pe[8 * c + 6], pe[8 * c + 7]));
 }
 
-__global__ void __launch_bounds__(kThreadsB, 2)
+template <int NL, int WG>
+__global__ void __launch_bounds__(Layout<WG>::kThreads, Layout<WG>::kMinBlocks)
 render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P, long long pixel_offset,
-                   float4* __restrict__ out) {
+                   const float4* __restrict__ envs, float4* __restrict__ out) {
+  constexpr int kThreadsB = Layout<WG>::kThreads;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
@@ -316,9 +324,9 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   float4* red = reinterpret_cast<float4*>(wgb + WG_FPIX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WG_MISC);
   float4* carry_s = reinterpret_cast<float4*>(wgb + WG_MISC + 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SM_TMEMSLOT);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Layout<WG>::kTmemSlot);
 
-  // ---- CTA set-up: weights and biases into shared memory, TMEM, barriers
+  // ---- CTA set-up: weights into shared memory, TMEM, barriers
   for (int i = tid; i < WBF16_BYTES / 16; i += kThreadsB)
     reinterpret_cast<uint4*>(Wsm)[i] = __ldg(reinterpret_cast<const uint4*>(m.wbf16) + i);
   if (t == 0) {
@@ -328,7 +336,7 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   fence_async_smem();
   if (warp == 0 && wg == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(kTmemCols)
+                 "r"(Layout<WG>::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -342,18 +350,19 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   const uint32_t X_s = smem_u32(X), H_s = smem_u32(H), W_s = smem_u32(Wsm);
 
   const int N = m.N, M = m.M;
+  const int env_hw = m.env_h * m.env_w;
   const float4* pos4 = reinterpret_cast<const float4*>(gb.pos);
   const float4* nrm4 = reinterpret_cast<const float4*>(gb.normal);
   const float4* view4 = reinterpret_cast<const float4*>(gb.view);
   const float4* ar4 = reinterpret_cast<const float4*>(gb.albedo_rough);
 
-  const long long workers = (long long)gridDim.x * kWG;
-  const long long worker = (long long)blockIdx.x * kWG + wg;
+  const long long workers = (long long)gridDim.x * WG;
+  const long long worker = (long long)blockIdx.x * WG + wg;
   const long long p0 = (long long)P * worker / workers, p1 = (long long)P * (worker + 1) / workers;
   const long long s_end = p1 * N;
   uint32_t phase = 0;
   int abort = 0;
-  if (t == 0) *carry_s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (t < NL) carry_s[t] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // One MMA round trip: barrier with an abort vote, issue by thread 0,
   // commit, bounded wait.  A wait that gives up only raises `abort`; the
@@ -431,8 +440,10 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
     const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
     // Eq. 1 factors of the primary direction, fetched before the MMAs so the
     // env-map loads overlap them
-    const f3 le1 = env_lookup_fast(m.env, m.env_h, m.env_w, wi);
+    const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
     const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+    f3 le1 = mk(0.f, 0.f, 0.f);
+    if (NL == 1) le1 = env_fetch(envs, tap1);
     {
       const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
 #pragma unroll
@@ -454,6 +465,18 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
       tdep = depth_fast(z[1], m.near_t, m.far_t);
     }
+    // Radiance is linear in the environment map: each light's contribution of
+    // this row is fr1 (v Lenv(w_i) + (1 - v) (pi/M) sum_j v'_j fr2_j Lenv(w'_j)).
+    f3 c[NL];
+    {
+      const f3 w0 = fr1 * v;
+      if (NL == 1) {
+        c[0] = w0 * le1;
+      } else {
+#pragma unroll
+        for (int e = 0; e < NL; ++e) c[e] = w0 * env_fetch(envs + e * env_hw, tap1);
+      }
+    }
 
     // (d) bounce: x' = x + t w_i; f' = H(x') into chunks 0..3 of the A tile
     {
@@ -461,7 +484,7 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       uint32_t fq[16];
       encode_point_bf16(m.grid, x2, fq);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) st_chunk(X, t, c, fq[4 * c], fq[4 * c + 1], fq[4 * c + 2], fq[4 * c + 3]);
+      for (int cc = 0; cc < 4; ++cc) st_chunk(X, t, cc, fq[4 * cc], fq[4 * cc + 1], fq[4 * cc + 2], fq[4 * cc + 3]);
     }
 
     // (b) B(f')
@@ -479,13 +502,16 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       r2 = 0.09f + 0.91f * sigmoid_fast(y[6]);
     }
     const f3 wo2 = neg(wi);
+    const float wsec = (1.0f - v) * (kPi / (float)M);
 
     // (c) + (e) at x': M directions about n'
-    f3 lo2 = mk(0.f, 0.f, 0.f);
     bool ok = true;
     for (int j = 0; j < M && ok; ++j) {
       const f3 wj = cosine_direction_fast(n2, m.seed, dir_counter(q, M, 1 + j));
-      const f3 lefr = env_lookup_fast(m.env, m.env_h, m.env_w, wj) * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+      const EnvTap tapj = env_tap_fast(m.env_h, m.env_w, wj);
+      const f3 frw = fr1 * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+      f3 lej = mk(0.f, 0.f, 0.f);
+      if (NL == 1) lej = env_fetch(envs, tapj);
       store_pe_bf16(X, t, wj);
       ok = run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); });
       if (!ok) break;
@@ -495,49 +521,55 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       float z0[1];
       head_fp32<1, 2>(D2 + lane_off, hp.ib2, &hp.iw3[0][0], hp.ib3, z0);
       const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(z0[0]);
-      lo2 = lo2 + lefr * v2;
+      const f3 wj3 = frw * (wsec * v2);
+      if (NL == 1) {
+        c[0] = c[0] + wj3 * lej;
+      } else {
+#pragma unroll
+        for (int e = 0; e < NL; ++e) c[e] = c[e] + wj3 * env_fetch(envs + e * env_hw, tapj);
+      }
     }
     if (!ok) break;
-    lo2 = lo2 * (kPi / (float)M);
 
-    // Eq. 2 and the primary term of Eq. 1
-    const f3 li = le1 * v + lo2 * (1.0f - v);
-    f3 c = li * fr1;
-    if (!valid) c = mk(0.f, 0.f, 0.f);
-
-    // deterministic segmented reduction of the tile's rows into its pixels
+    // deterministic segmented reduction of the tile's rows into their pixels,
+    // one light at a time
     const int key = valid ? ps : -1;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const float ox = __shfl_down_sync(0xffffffffu, c.x, off);
-      const float oy = __shfl_down_sync(0xffffffffu, c.y, off);
-      const float oz = __shfl_down_sync(0xffffffffu, c.z, off);
-      const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
-      if (lane + off < 32 && ok2 == key) c = mk(c.x + ox, c.y + oy, c.z + oz);
-    }
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const bool head = lane == 0 || prev != key;
-    wg_sync(wg);   // fpix reads are done before red (same bytes) is written
-    red[t] = head ? make_float4(c.x, c.y, c.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-    wg_sync(wg);
-    if (t < npix) {
-      const int ra = max(0, t * N - off0);
-      const int rb = min(nvalid, (t + 1) * N - off0);
-      f3 sum = mk(0.f, 0.f, 0.f);
-      if (t == 0) {
-        const float4 cs = *carry_s;
-        sum = mk(cs.x, cs.y, cs.z);
+#pragma unroll
+    for (int e = 0; e < NL; ++e) {
+      f3 ce = valid ? c[e] : mk(0.f, 0.f, 0.f);
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float ox = __shfl_down_sync(0xffffffffu, ce.x, off);
+        const float oy = __shfl_down_sync(0xffffffffu, ce.y, off);
+        const float oz = __shfl_down_sync(0xffffffffu, ce.z, off);
+        const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+        if (lane + off < 32 && ok2 == key) ce = mk(ce.x + ox, ce.y + oy, ce.z + oz);
       }
-      for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
-        const float4 h = red[r];
-        sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
+      wg_sync(wg);   // fpix reads (first light) or the previous light's sums are done
+      red[t] = head ? make_float4(ce.x, ce.y, ce.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      wg_sync(wg);
+      if (t < npix) {
+        const int ra = max(0, t * N - off0);
+        const int rb = min(nvalid, (t + 1) * N - off0);
+        f3 sum = mk(0.f, 0.f, 0.f);
+        if (t == 0) {
+          const float4 cs = carry_s[e];
+          sum = mk(cs.x, cs.y, cs.z);
+        }
+        for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
+          const float4 h = red[r];
+          sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
+        }
+        const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
+        if (complete) {
+          const float sc = kPi / (float)N;
+          out[(long long)e * P + p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
+        }
+        if (t == npix - 1)
+          carry_s[e] = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
       }
-      const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
-      if (complete) {
-        const float sc = kPi / (float)N;
-        out[p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
-      }
-      if (t == npix - 1) *carry_s = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
     }
     wg_sync(wg);
   }
@@ -549,21 +581,77 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   __syncthreads();
   tc_fence_after();
   if (warp == 0 && wg == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(Layout<WG>::kTmemCols)
+                 : "memory");
+}
+
+template <int NL, int WG>
+cudaError_t prepare_variant() {
+  return cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Layout<WG>::kSmem);
+}
+
+template <int NL, int WG>
+cudaError_t launch_variant(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P, long long offset,
+                           const float4* envs, float4* out, int num_sms, cudaStream_t s) {
+  const long long per_sm = Layout<WG>::kMinBlocks;
+  const long long want = ((long long)P + WG - 1) / WG;
+  const int grid = (int)(want < per_sm * num_sms ? want : per_sm * num_sms);
+  render_bf16_kernel<NL, WG><<<grid, Layout<WG>::kThreads, Layout<WG>::kSmem, s>>>(m, hp, gb, P, offset, envs, out);
+  return cudaGetLastError();
+}
+
+template <int WG>
+cudaError_t launch_lights(int nl, const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
+                          long long offset, const float4* envs, float4* out, int num_sms, cudaStream_t s) {
+  switch (nl) {
+    case 8: return launch_variant<8, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    case 4: return launch_variant<4, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    case 2: return launch_variant<2, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    default: return launch_variant<1, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
+  }
 }
 
 }  // namespace
 
 cudaError_t prepare_render_bf16() {
-  return cudaFuncSetAttribute(render_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAlloc);
+  cudaError_t e = cudaSuccess;
+  e = e != cudaSuccess ? e : prepare_variant<1, 1>();
+  e = e != cudaSuccess ? e : prepare_variant<2, 1>();
+  e = e != cudaSuccess ? e : prepare_variant<4, 1>();
+  e = e != cudaSuccess ? e : prepare_variant<8, 1>();
+  e = e != cudaSuccess ? e : prepare_variant<1, 2>();
+  e = e != cudaSuccess ? e : prepare_variant<2, 2>();
+  e = e != cudaSuccess ? e : prepare_variant<4, 2>();
+  e = e != cudaSuccess ? e : prepare_variant<8, 2>();
+  return e;
+}
+
+// E lights in launches of up to `max_nl` (1, 2, 4 or 8) lights each; light e
+// reads envs + e * env_h * env_w and writes out + e * P.  Every launch
+// recomputes the geometry, so fewer, wider launches share more work.
+cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
+                                      long long offset, const float4* envs, int E, float4* out, int num_sms,
+                                      int max_nl, int wg, cudaStream_t s) {
+  const long long hw = (long long)m.env_h * m.env_w;
+  for (int e0 = 0; e0 < E;) {
+    int nl = 1;
+    while (nl * 2 <= max_nl && nl * 2 <= E - e0) nl *= 2;
+    ModelDesc mm = m;
+    mm.env = envs + e0 * hw;
+    const cudaError_t err = wg == 1 ? launch_lights<1>(nl, mm, hp, gb, P, offset, envs + e0 * hw,
+                                                       out + (long long)e0 * P, num_sms, s)
+                                    : launch_lights<2>(nl, mm, hp, gb, P, offset, envs + e0 * hw,
+                                                       out + (long long)e0 * P, num_sms, s);
+    if (err != cudaSuccess) return err;
+    e0 += nl;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                long long offset, float4* out, int num_sms, cudaStream_t s) {
-  const long long want = ((long long)P + kWG - 1) / kWG;
-  const int grid = (int)(want < 2LL * num_sms ? want : 2LL * num_sms);
-  render_bf16_kernel<<<grid, kThreadsB, kSmemAlloc, s>>>(m, hp, gb, P, offset, out);
-  return cudaGetLastError();
+  return launch_variant<1, 2>(m, hp, gb, P, offset, m.env, out, num_sms, s);
 }
 
 }  // namespace rtk

@@ -106,6 +106,9 @@ cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int l
 cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s);
 cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                long long offset, float4* out, int num_sms, cudaStream_t s);
+cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
+                                      long long offset, const float4* envs, int E, float4* out, int num_sms,
+                                      int max_nl, int wg, cudaStream_t s);
 // Status-word codes: (kStatusTimeout | where) after a bounded wait gave up.
 constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,

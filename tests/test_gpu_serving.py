@@ -1,0 +1,97 @@
+"""Batched lights (rt_render_frame_multi), the launch-shape autotuner and the CUDA-graph batch."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+from oracle import render as orender
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_10327_gb300 import build
+    build.build()
+    from paper_2409_10327_gb300 import binding
+    return binding
+
+
+def _envs(cfg, n, seed0=100):
+    return np.stack([scenegen.make_env(cfg.env_h, cfg.env_w, seed0 + e) for e in range(n)])
+
+
+def _single_light(cfg, sc, gb, env, offset=0, shape=None):
+    sc2 = scenegen.Scene(cfg, sc.table, sc.brdf, sc.irt, env)
+    r = helpers.renderer_for(cfg, sc2)
+    if shape is not None and cfg.precision == "bf16":
+        r.set_launch_shape(1, shape[1])
+    return r.render_frame(gb, pixel_offset=offset).cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_multi_light_equals_single_light_renders(lib, precision):
+    cfg = helpers.small_cfg(n_dirs=48, m_dirs=4, precision=precision)
+    sc = scenegen.make_scene(cfg, 0, bias_scale=0.1)
+    gb = helpers.to_cuda(scenegen.make_gbuffer(150, 5))
+    envs = _envs(cfg, 5)
+    r = helpers.renderer_for(cfg, sc)
+    denv = torch.from_numpy(envs).cuda()
+    shapes = [(nl, wg) for nl in (1, 2, 4, 8) for wg in (1, 2)] if precision == "bf16" else [None]
+    for shape in shapes:
+        if shape is not None:
+            r.set_launch_shape(*shape)
+        out = r.render_frame_multi(gb, denv, pixel_offset=7).cpu().numpy()
+        for e in range(5):
+            ref = _single_light(cfg, sc, gb, envs[e], 7, shape)
+            assert helpers.rel_err(out[e, :, :3], ref[:, :3]) <= 1e-5, (shape, e)
+            assert np.all(out[e, :, 3] == 0)
+
+
+def test_tuner_picks_a_shape_and_reproduces_it(lib):
+    cfg = helpers.small_cfg(n_dirs=64, m_dirs=8, precision="bf16")
+    sc = scenegen.make_scene(cfg, 1)
+    gb = helpers.to_cuda(scenegen.make_gbuffer(2000, 6))
+    denv = torch.from_numpy(_envs(cfg, 8)).cuda()
+    r = helpers.renderer_for(cfg, sc)
+    best = r.tune(gb, denv)
+    nl, wg = r.launch_shape()
+    assert best > 0 and nl in (1, 2, 4, 8) and wg in (1, 2)
+    tuned = r.render_frame_multi(gb, denv).cpu().numpy()
+    r.set_launch_shape(1, 2)
+    ref = r.render_frame_multi(gb, denv).cpu().numpy()
+    assert helpers.rel_err(tuned[..., :3], ref[..., :3]) <= 1e-5
+
+
+def test_graph_batch_matches_eager(lib):
+    from paper_2409_10327_gb300 import serve
+    cfg = helpers.small_cfg(n_dirs=32, m_dirs=8, precision="bf16")
+    sc = scenegen.make_scene(cfg, 2)
+    r = helpers.renderer_for(cfg, sc)
+    gbs = [helpers.to_cuda(scenegen.make_gbuffer(300, 10 + v)) for v in range(3)]
+    srv = serve.BatchedServer(r, gbs, torch.from_numpy(_envs(cfg, 3)).cuda())
+    eager = srv.render_eager().clone()
+    srv.capture()
+    srv.out.zero_()
+    got = srv.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(got, eager)
+    lat = srv.view_latencies_ms()
+    assert len(lat) == 3 and all(x > 0 for x in lat)
+
+
+def test_multi_light_bf16_against_oracle(lib):
+    cfg = scenegen.CONFIGS["tiny64"]
+    cfg = type(cfg)(**{**cfg.__dict__, "precision": "bf16"})
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    envs = _envs(cfg, 3)
+    r = helpers.renderer_for(cfg, sc)
+    out = r.render_frame_multi(helpers.to_cuda(gb), torch.from_numpy(envs).cuda()).cpu().numpy()
+    for e in range(3):
+        prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, envs[e])
+        opt = helpers.oracle_options(cfg)
+        ref = orender.render(gb, prm, opt)
+        sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=4, mlp=True)
+        ok, stats = helpers.bf16_parity(out[e, :, :3], ref, sens)
+        assert ok and stats["psnr_db"] >= helpers.BF16_PSNR_MIN, (e, stats)
