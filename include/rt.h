@@ -204,15 +204,16 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
  * lights per launch on one shared geometry pass (hash encodes, both MLPs,
  * bounce): each row contributes fr1 (v Lenv(w_i) + (1 - v) (pi/M) sum_j v'_j
  * fr2_j Lenv(w'_j)) to every light.  Lights per launch (1, 2, 4, 8) and
- * warpgroups per CTA (1 or 2) follow the context's launch shape (rt_tune /
- * rt_set_launch_shape; default 8 and 2).  The FP32 path renders one light
+ * warpgroups per CTA (2: two CTAs per SM; 3 or 4: one CTA per SM) follow the
+ * context's launch shape (rt_tune / rt_set_launch_shape; default 8 and 3),
+ * which rt_render_frame (one light) also uses.  The FP32 path renders one light
  * per pass.  Equal, light by light, to rt_render_frame with that map bound.
  * E in 0..1024.  No allocation, no synchronisation: capturable. */
 rt_status rt_render_frame_multi(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                                 const float* envs, int32_t E, float* radiance, void* stream);
 
 /* Autotuner of rt_render_frame_multi's launch shape: times every shape (lights
- * per launch 1/2/4/8 up to E, warpgroups per CTA 1/2) once after a warm-up on
+ * per launch 1/2/4/8 up to E, warpgroups per CTA 2/3/4) once after a warm-up on
  * this workload, writing radiance as rt_render_frame_multi does, keeps the
  * fastest in the context and returns its time in *best_ms (may be NULL; -1
  * for the FP32 path, which has one shape).  Synchronises `stream`. */
@@ -220,7 +221,7 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
                   float* radiance, void* stream, float* best_ms);
 
 /* Read or force the BF16 launch shape (lights_per_launch in {1,2,4,8},
- * warpgroups in {1,2}; anything else is RT_ERR_INVALID_ARG). */
+ * warpgroups in {2,3,4}; anything else is RT_ERR_INVALID_ARG). */
 rt_status rt_tuned_shape(const rt_ctx* ctx, int32_t* lights_per_launch, int32_t* warpgroups);
 rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t warpgroups);
 

@@ -23,7 +23,7 @@ struct rt_ctx {
   HeadParams head;     // host copy of the FP32 biases / output layers (BF16 kernel parameter)
   bool ready;
   int tuned_nl;        // lights per launch of the BF16 kernel (rt_tune), default 8
-  int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 2
+  int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 3
 };
 
 namespace {
@@ -182,7 +182,7 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
   if (ctx == nullptr) return RT_ERR_OOM;
   ctx->cfg = *cfg;
   ctx->tuned_nl = 8;
-  ctx->tuned_wg = 2;
+  ctx->tuned_wg = 3;
   for (int l = 0; l < cfg->levels; ++l) {
     ctx->res[l] = level_res(cfg, l);
     ctx->dense[l] = level_dense(cfg, ctx->res[l]) ? 1 : 0;
@@ -407,7 +407,7 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
   float best = 3.0e38f;
   int best_nl = ctx->tuned_nl, best_wg = ctx->tuned_wg;
   st = RT_OK;
-  for (int wg = 1; wg <= 2 && st == RT_OK; ++wg) {
+  for (int wg = 2; wg <= 4 && st == RT_OK; ++wg) {
     for (int nl = 1; nl <= 8 && st == RT_OK; nl *= 2) {
       if (nl > 1 && nl / 2 >= E) break;   // wider launches than E lights repeat the previous shape
       float ms = 0.0f;
@@ -445,7 +445,7 @@ rt_status rt_tuned_shape(const rt_ctx* ctx, int32_t* lights_per_launch, int32_t*
 rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t warpgroups) {
   if (ctx == nullptr) return RT_ERR_INVALID_ARG;
   const int nl = lights_per_launch;
-  if (!(nl == 1 || nl == 2 || nl == 4 || nl == 8) || !(warpgroups == 1 || warpgroups == 2)) return RT_ERR_INVALID_ARG;
+  if (!(nl == 1 || nl == 2 || nl == 4 || nl == 8) || warpgroups < 2 || warpgroups > 4) return RT_ERR_INVALID_ARG;
   ctx->tuned_nl = nl;
   ctx->tuned_wg = warpgroups;
   return RT_OK;

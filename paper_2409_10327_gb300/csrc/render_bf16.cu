@@ -32,45 +32,69 @@
 namespace rtk {
 
 // ---- BF16 weight image (runs after the FP32 repack on the same stream) -----
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// One thread per bf16 element of the image.
 __global__ void repack_bf16_kernel(const float* __restrict__ wp, uint8_t* __restrict__ out) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // one element of a 64-wide row
-  const int total_rows = 64 + 64 + 16 + 64 + 64 + 16;
-  if (e >= total_rows * 64) return;
-  const int row = e / 64, k = e % 64;
-  float v = 0.0f;
-  int base, n;
-  if (row < 64) {                     // I layer 1: [f | PE]
-    base = OFFB_IW1; n = row;
-    v = k < 32 ? wp[OFF_IW1F + k * 64 + n] : wp[OFF_IW1P + (k - 32) * 64 + n];
-  } else if (row < 128) {
-    base = OFFB_IW2; n = row - 64;
-    v = wp[OFF_IW2 + k * 64 + n];
-  } else if (row < 144) {
-    base = OFFB_IW3; n = row - 128;
-    v = n < 2 ? wp[OFF_IW3 + k * 2 + n] : 0.0f;
-  } else if (row < 208) {
-    base = OFFB_BW1; n = row - 144;
-    v = k < 32 ? wp[OFF_BW1 + k * 64 + n] : 0.0f;
-  } else if (row < 272) {
-    base = OFFB_BW2; n = row - 208;
-    v = wp[OFF_BW2 + k * 64 + n];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= WBF16_BYTES / 2) return;
+  const int byte = 2 * e;
+  __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+  if (byte < OFFB_IB2) {
+    // one of the four 64 x 64 swizzled matrices: invert swz128
+    const int tile = byte / 8192, o = byte % 8192;
+    const int n = (o / 1024) * 8 + (o % 1024) / 128;
+    const int chunk = ((o % 128) / 16) ^ (n & 7);
+    const int k = chunk * 8 + (o % 16) / 2;
+    float f = 0.0f;
+    if (tile == 0) {                                    // I layer 1: [f | PE | 1 | 1 | 0]
+      if (k < 32) f = wp[OFF_IW1F + k * 64 + n];
+      else if (k < kBiasCol) f = wp[OFF_IW1P + (k - 32) * 64 + n];
+    } else if (tile == 1) {
+      f = wp[OFF_IW2 + k * 64 + n];
+    } else if (tile == 2) {                             // B layer 1: [f | 0 | b1]
+      if (k < 32) f = wp[OFF_BW1 + k * 64 + n];
+    } else {
+      f = wp[OFF_BW2 + k * 64 + n];
+    }
+    v = __float2bfloat16_rn(f);
+    if (tile == 0 || tile == 2) {
+      const float b = tile == 0 ? wp[OFF_IB1 + n] : wp[OFF_BB1 + n];
+      __nv_bfloat16 hi, lo;
+      split_bf16(b, hi, lo);
+      if (k == kBiasCol) v = hi;
+      if (k == kBiasCol + 1) v = lo;
+    }
+  } else if (byte < OFFB_ONES) {
+    // layer-2 bias tiles: row n = 8 x hi/8, 8 x lo/8 (exact scalings by 1/8)
+    const int tile = (byte - OFFB_IB2) / 2048, o = (byte - OFFB_IB2) % 2048;
+    const int n = o / 32, k = (o % 32) / 2;
+    const float b = tile == 0 ? wp[OFF_IB2 + n] : wp[OFF_BB2 + n];
+    __nv_bfloat16 hi, lo;
+    split_bf16(b, hi, lo);
+    v = __float2bfloat16_rn(0.125f * __bfloat162float(k < 8 ? hi : lo));
   } else {
-    base = OFFB_BW3; n = row - 272;
-    v = n < 7 ? wp[OFF_BW3 + k * 8 + n] : 0.0f;
+    v = __float2bfloat16_rn(1.0f);                      // the all-ones tile
   }
-  *reinterpret_cast<__nv_bfloat16*>(out + base + swz128(n, k)) = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16*>(out + byte) = v;
 }
 
 cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s) {
-  repack_bf16_kernel<<<(288 * 64 + 255) / 256, 256, 0, s>>>(wpack, wbf16);
+  repack_bf16_kernel<<<(WBF16_BYTES / 2 + 255) / 256, 256, 0, s>>>(wpack, wbf16);
   return cudaGetLastError();
 }
 
 namespace {
 
-// Kernel variants: NL lights per launch (1, 2, 4, 8), WG warpgroups per CTA
-// (1: three CTAs per SM; 2: two CTAs per SM).  Each warpgroup owns 128 TMEM
-// columns: D1 = [0, 64), D2 = [64, 128).
+// Kernel variants: NL lights per launch (1, 2, 4, 8) and WG warpgroups per
+// CTA: 2 (two CTAs per SM) or 3 and 4 (one CTA per SM, one shared copy of the
+// weights, and the shared-memory carveout kept to what the CTA needs so that
+// the rest of the SM's 256 KB serves as L1 for the environment maps and the
+// coarse hash levels).  Each warpgroup owns 128 TMEM columns: D1 = [0, 64),
+// D2 = [64, 128).
 constexpr int kPixSlots = 34;                // pixels touched by one tile when N >= 4
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int SM_W = 0;
@@ -86,10 +110,12 @@ static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
 template <int WG>
 struct Layout {
   static constexpr int kThreads = 128 * WG;
-  static constexpr int kTmemCols = 128 * WG;
+  static constexpr int kTmemCols = WG <= 2 ? 128 * WG : 512;   // allocations are powers of two
   static constexpr int kTmemSlot = SM_WG + WG * WG_BYTES;
   static constexpr size_t kSmem = kTmemSlot + 16 + 1024;
-  static constexpr int kMinBlocks = WG == 1 ? 3 : 2;
+  static constexpr int kMinBlocks = WG <= 2 ? 2 : 1;
+  // smallest carveout (percent of the 228 KB maximum) that holds kMinBlocks CTAs
+  static constexpr int kCarveout = (int)((kMinBlocks * (kSmem + 1024) * 100 + 233471) / 233472);
 };
 
 constexpr uint32_t idesc_bf16(int M, int N) {
@@ -107,6 +133,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// K-major, 32-byte swizzle, 8-row groups 256 bytes apart (the K = 16 bias tiles).
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
   return d;
 }
 
@@ -199,9 +236,20 @@ __device__ __forceinline__ void st_chunk(uint8_t* tile, int row, int chunk, uint
 __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_s, uint32_t b_s, int ksteps, uint32_t idesc) {
   for (int k = 0; k < ksteps; ++k) mma_bf16(d, sdesc(a_s + 32 * k), sdesc(b_s + 32 * k), idesc, k > 0 ? 1u : 0u);
 }
+// layer 2: D <- H . W2^T + ones . Bias2^T
+__device__ __forceinline__ void mma_layer2(uint32_t d, uint32_t h_s, uint32_t w_s, uint32_t ones_s, uint32_t bias_s) {
+  mma_chain(d, h_s, w_s, 4, kIdescN64);
+  mma_bf16(d, sdesc32(ones_s), sdesc32(bias_s), kIdescN64, 1u);
+}
+// B's layer 1: f' (k-steps 0, 1) and the bias columns (k-step 3; B's weights are zero on the PE columns)
+__device__ __forceinline__ void mma_brdf_layer1(uint32_t d, uint32_t x_s, uint32_t w_s) {
+  mma_bf16(d, sdesc(x_s), sdesc(w_s), kIdescN64, 0u);
+  mma_bf16(d, sdesc(x_s + 32), sdesc(w_s + 32), kIdescN64, 1u);
+  mma_bf16(d, sdesc(x_s + 96), sdesc(w_s + 96), kIdescN64, 1u);
+}
 
-// hidden epilogue: H[row] = bf16(relu(D[row][0:64] + bias))
-__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bias, uint8_t* H, int row) {
+// hidden epilogue: H[row] = bf16(relu(D[row][0:64])) (the bias is already in D)
+__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, uint8_t* H, int row) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t r[32];
@@ -212,19 +260,16 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t taddr, const float* bia
       uint32_t q[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int col = 32 * h + 8 * c + 2 * e;
-        q[e] = pack_relu_bf16(__uint_as_float(r[8 * c + 2 * e]) + bias[col],
-                              __uint_as_float(r[8 * c + 2 * e + 1]) + bias[col + 1]);
+        q[e] = pack_relu_bf16(__uint_as_float(r[8 * c + 2 * e]), __uint_as_float(r[8 * c + 2 * e + 1]));
       }
       st_chunk(H, row, 4 * h + c, q[0], q[1], q[2], q[3]);
     }
   }
 }
 
-// Output layer in FP32: z[o] = b3[o] + sum_k relu(D[row][k] + b2[k]) W3[k][o]
+// Output layer in FP32: z[o] = b3[o] + sum_k relu(D[row][k]) W3[k][o] (b2 is already in D)
 template <int NOUT, int LDW>
-__device__ __forceinline__ void head_fp32(uint32_t taddr, const float* b2, const float* W3, const float* b3,
-                                          float (&z)[NOUT]) {
+__device__ __forceinline__ void head_fp32(uint32_t taddr, const float* W3, const float* b3, float (&z)[NOUT]) {
 #pragma unroll
   for (int o = 0; o < NOUT; ++o) z[o] = b3[o];
 #pragma unroll
@@ -234,7 +279,7 @@ __device__ __forceinline__ void head_fp32(uint32_t taddr, const float* b2, const
     tmem_ld_wait();
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-      const float a = fmaxf(__uint_as_float(r[k]) + b2[32 * h + k], 0.0f);
+      const float a = fmaxf(__uint_as_float(r[k]), 0.0f);
 #pragma unroll
       for (int o = 0; o < NOUT; ++o) z[o] = fmaf(a, W3[(32 * h + k) * LDW + o], z[o]);
     }
@@ -295,12 +340,13 @@ __device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint3
   }
 }
 
-// PE(w) as bf16 into chunks 4..7 of the A tile row (27 values, then zeros)
+// PE(w) as bf16 into chunks 4..7 of the A tile row: 27 values, then the two
+// 1.0 columns that carry layer 1's bias, then zeros
 __device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
   float pe[32];
   positional_encoding_fast(w, [&](int k, float v) { pe[k] = v; });
 #pragma unroll
-  for (int k = kPE; k < 32; ++k) pe[k] = 0.0f;
+  for (int k = kPE; k < 32; ++k) pe[k] = (k == kBiasCol - 32 || k == kBiasCol - 31) ? 1.0f : 0.0f;
 #pragma unroll
   for (int c = 0; c < 4; ++c)
     st_chunk(X, row, 4 + c, pack_bf16(pe[8 * c], pe[8 * c + 1]), pack_bf16(pe[8 * c + 2], pe[8 * c + 3]),
@@ -456,12 +502,12 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
 
     // (c) I(f, w_i)
     if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); })) break;
-    epilogue_hidden(D1 + lane_off, hp.ib1, H, t);
-    if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); })) break;
+    epilogue_hidden(D1 + lane_off, H, t);
+    if (!run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
     float v, tdep;
     {
       float z[2];
-      head_fp32<2, 2>(D2 + lane_off, hp.ib2, &hp.iw3[0][0], hp.ib3, z);
+      head_fp32<2, 2>(D2 + lane_off, &hp.iw3[0][0], hp.ib3, z);
       v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
       tdep = depth_fast(z[1], m.near_t, m.far_t);
     }
@@ -488,14 +534,14 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
     }
 
     // (b) B(f')
-    if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_BW1, 2, kIdescN64); })) break;
-    epilogue_hidden(D1 + lane_off, hp.bb1, H, t);
-    if (!run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_BW2, 4, kIdescN64); })) break;
+    if (!run_mma([&] { mma_brdf_layer1(D1, X_s, W_s + OFFB_BW1); })) break;
+    epilogue_hidden(D1 + lane_off, H, t);
+    if (!run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) break;
     f3 n2, a2;
     float r2;
     {
       float y[7];
-      head_fp32<7, 8>(D2 + lane_off, hp.bb2, &hp.bw3[0][0], hp.bb3, y);
+      head_fp32<7, 8>(D2 + lane_off, &hp.bw3[0][0], hp.bb3, y);
       const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
       n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
       a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
@@ -515,11 +561,11 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       store_pe_bf16(X, t, wj);
       ok = run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); });
       if (!ok) break;
-      epilogue_hidden(D1 + lane_off, hp.ib1, H, t);
-      ok = run_mma([&] { mma_chain(D2, H_s, W_s + OFFB_IW2, 4, kIdescN64); });
+      epilogue_hidden(D1 + lane_off, H, t);
+      ok = run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
       if (!ok) break;
       float z0[1];
-      head_fp32<1, 2>(D2 + lane_off, hp.ib2, &hp.iw3[0][0], hp.ib3, z0);
+      head_fp32<1, 2>(D2 + lane_off, &hp.iw3[0][0], hp.ib3, z0);
       const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(z0[0]);
       const f3 wj3 = frw * (wsec * v2);
       if (NL == 1) {
@@ -587,8 +633,11 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
 
 template <int NL, int WG>
 cudaError_t prepare_variant() {
-  return cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Layout<WG>::kSmem);
+  cudaError_t e = cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Layout<WG>::kSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              Layout<WG>::kCarveout);
 }
 
 template <int NL, int WG>
@@ -614,16 +663,19 @@ cudaError_t launch_lights(int nl, const ModelDesc& m, const HeadParams& hp, cons
 
 }  // namespace
 
+template <int WG>
+cudaError_t prepare_wg() {
+  cudaError_t e = prepare_variant<1, WG>();
+  e = e != cudaSuccess ? e : prepare_variant<2, WG>();
+  e = e != cudaSuccess ? e : prepare_variant<4, WG>();
+  e = e != cudaSuccess ? e : prepare_variant<8, WG>();
+  return e;
+}
+
 cudaError_t prepare_render_bf16() {
-  cudaError_t e = cudaSuccess;
-  e = e != cudaSuccess ? e : prepare_variant<1, 1>();
-  e = e != cudaSuccess ? e : prepare_variant<2, 1>();
-  e = e != cudaSuccess ? e : prepare_variant<4, 1>();
-  e = e != cudaSuccess ? e : prepare_variant<8, 1>();
-  e = e != cudaSuccess ? e : prepare_variant<1, 2>();
-  e = e != cudaSuccess ? e : prepare_variant<2, 2>();
-  e = e != cudaSuccess ? e : prepare_variant<4, 2>();
-  e = e != cudaSuccess ? e : prepare_variant<8, 2>();
+  cudaError_t e = prepare_wg<2>();
+  e = e != cudaSuccess ? e : prepare_wg<3>();
+  e = e != cudaSuccess ? e : prepare_wg<4>();
   return e;
 }
 
@@ -639,10 +691,11 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
     while (nl * 2 <= max_nl && nl * 2 <= E - e0) nl *= 2;
     ModelDesc mm = m;
     mm.env = envs + e0 * hw;
-    const cudaError_t err = wg == 1 ? launch_lights<1>(nl, mm, hp, gb, P, offset, envs + e0 * hw,
-                                                       out + (long long)e0 * P, num_sms, s)
-                                    : launch_lights<2>(nl, mm, hp, gb, P, offset, envs + e0 * hw,
-                                                       out + (long long)e0 * P, num_sms, s);
+    const float4* ee = envs + e0 * hw;
+    float4* oo = out + (long long)e0 * P;
+    const cudaError_t err = wg == 2   ? launch_lights<2>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
+                            : wg == 4 ? launch_lights<4>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
+                                      : launch_lights<3>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s);
     if (err != cudaSuccess) return err;
     e0 += nl;
   }
@@ -651,7 +704,7 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 
 cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                long long offset, float4* out, int num_sms, cudaStream_t s) {
-  return launch_variant<1, 2>(m, hp, gb, P, offset, m.env, out, num_sms, s);
+  return launch_variant<1, 3>(m, hp, gb, P, offset, m.env, out, num_sms, s);
 }
 
 }  // namespace rtk

@@ -35,18 +35,27 @@ constexpr int OFF_BB3 = OFF_BW3 + 64 * 8;        // [8]
 constexpr int WPACK_FLOATS = OFF_BB3 + 8;
 static_assert(OFF_BW1 % 4 == 0 && OFF_BW3 % 4 == 0 && WPACK_FLOATS % 4 == 0, "float4 alignment");
 
-// BF16 weight image for the tensor-core path (bytes).  Each matrix is stored
-// as [N rows = outputs][K = 64 inputs] bf16, K-major, in the 128-byte swizzle
-// of tcgen05 shared-memory descriptors: element (n, k) of a tile lives at
-// (n/8)*1024 + (n%8)*128 + (((2k)/16) ^ (n%8))*16 + (2k)%16.
-// I layer 1 takes [f (32, zero beyond L*F) | PE (27) | 0 (5)].
+// BF16 weight image for the tensor-core path (bytes).  The 64 x 64 matrices
+// are stored as [N rows = outputs][K = 64 inputs] bf16, K-major, in the
+// 128-byte swizzle of tcgen05 shared-memory descriptors: element (n, k) of a
+// tile lives at (n/8)*1024 + (n%8)*128 + (((2k)/16) ^ (n%8))*16 + (2k)%16.
+// Layer-1 biases ride in the A tile: its columns 59 and 60 hold 1.0, and
+// columns 59/60 of I's and B's layer-1 tiles hold the bf16 hi/lo split of b1
+// (B's layer 1 reads K-steps 0, 1 and 3).  Layer-2 biases come from one more
+// K = 16 MMA of a constant all-ones tile [128 x 16] against a bias tile
+// [64 x 16] whose row n holds 8 x hi/8 and 8 x lo/8 of b2[n] (both tiles in
+// the 32-byte swizzle, 32-byte rows, 8-row groups 256 bytes apart; a row's
+// sum does not depend on how the swizzle permutes its two 16-byte halves).
+// I layer 1 takes [f (32, zero beyond L*F) | PE (27) | 1 | 1 | 0 (3)].
 constexpr int OFFB_IW1 = 0;        // 64 x 64
 constexpr int OFFB_IW2 = 8192;     // 64 x 64
-constexpr int OFFB_IW3 = 16384;    // 16 x 64 (rows 0..1 used)
-constexpr int OFFB_BW1 = 18432;    // 64 x 64 (k < L*F used)
-constexpr int OFFB_BW2 = 26624;    // 64 x 64
-constexpr int OFFB_BW3 = 34816;    // 16 x 64 (rows 0..6 used)
-constexpr int WBF16_BYTES = 36864;
+constexpr int OFFB_BW1 = 16384;    // 64 x 64 (k < L*F, and the bias columns)
+constexpr int OFFB_BW2 = 24576;    // 64 x 64
+constexpr int OFFB_IB2 = 32768;    // 64 x 16, 32-byte swizzle
+constexpr int OFFB_BB2 = 34816;    // 64 x 16, 32-byte swizzle
+constexpr int OFFB_ONES = 36864;   // 128 x 16 of 1.0, 32-byte swizzle
+constexpr int WBF16_BYTES = 40960;
+constexpr int kBiasCol = 59;       // A-tile / layer-1 columns carrying b1 (hi at 59, lo at 60)
 
 __host__ __device__ constexpr int swz128(int n, int k) {
   return (n >> 3) * 1024 + (n & 7) * 128 + ((((2 * k) >> 4) ^ (n & 7)) << 4) + ((2 * k) & 15);
