@@ -1,26 +1,29 @@
 // Fused BF16 tensor-core hot path: stages (a)-(e) of the hash renderer in one
 // persistent kernel (rt_render_frame with precision RT_BF16).
 //
-// Layout of the work.  A CTA holds two independent warpgroups.  Each
+// Layout of the work.  A CTA holds WG independent warpgroups.  Each
 // warpgroup owns a contiguous range of primary points and walks its
 // secondary samples (point p, direction i) in tiles of 128 consecutive
 // samples: thread t of the warpgroup owns row t of the tile, which is also
-// TMEM lane t of the warpgroup's accumulators.  Every MLP layer of the tile
-// is one chain of tcgen05.mma (M = 128, N = 64 or 16, K = 16 per
-// instruction) issued by one thread, with the A operand (activations, bf16)
-// and the B operand (weights, bf16) in 128-byte-swizzled shared memory and
-// the FP32 accumulator in tensor memory.  The epilogue reads the accumulator
-// with tcgen05.ld, adds the bias, applies ReLU and rounds to bf16 for the
-// next layer.  Hash interpolation, depth, shading and all sums stay in FP32;
-// the table is read as FP16.
+// TMEM lane t of the warpgroup's columns.  Every 64-wide MLP layer of the
+// tile is one chain of tcgen05.mma (M = 128, N = 64, K = 16 per instruction)
+// issued by one thread.  The A operand (the layer input, bf16) lives in
+// tensor memory next to the FP32 accumulator: threads write their rows with
+// tcgen05.st and the MMA reads them from TMEM, so activations never pass
+// through shared memory; the B operand (weights, bf16) sits in 128-byte-
+// swizzled shared memory, loaded once per CTA.  Layer biases ride on the
+// MMAs (a ones column in the layer-1 input, a ones tile times a bias tile
+// for layer 2), so the epilogue only applies ReLU, rounds to bf16 and
+// writes the next A operand.  Hash interpolation, depth, shading and all
+// sums stay in FP32; the table is read as FP16.
 //
 // Per tile: I on [f, PE(w_i)], the bounce and f' = H(x'), B on f', then for
 // each of the M secondary directions I on [f', PE(w'_j)] with f' kept in the
-// A tile, then Eq. 1 / Eq. 2 and a deterministic segmented reduction of the
-// rows into their pixels.  The two 64-wide layers of each MLP run on the
-// tensor cores; the narrow output layer (2 or 7 outputs) runs in FP32 on
-// the CUDA cores straight from the FP32 layer-2 accumulator, which saves a
-// round trip per MLP and keeps t and n' free of one bf16 rounding.
+// A operand, then Eq. 1 / Eq. 2 and a deterministic segmented reduction of
+// the rows into their pixels.  The narrow output layer (2 or 7 outputs)
+// runs in FP32 on the CUDA cores straight from the FP32 layer-2
+// accumulator, which saves a round trip per MLP and keeps t and n' free of
+// one bf16 rounding.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // warpgroup records kStatusTimeout in the status word and stops.
@@ -91,18 +94,22 @@ namespace {
 
 // Kernel variants: NL lights per launch (1, 2, 4, 8) and WG warpgroups per
 // CTA: 2 (two CTAs per SM) or 3 and 4 (one CTA per SM, one shared copy of the
-// weights, and the shared-memory carveout kept to what the CTA needs so that
-// the rest of the SM's 256 KB serves as L1 for the environment maps and the
-// coarse hash levels).  Each warpgroup owns 128 TMEM columns: D1 = [0, 64),
-// D2 = [64, 128).
+// weights).  Shared memory holds only the weights and a small block per
+// warpgroup, and the carveout is kept to that, so most of the SM's 256 KB
+// serves as L1 for the environment maps and the coarse hash levels.
+//
+// TMEM columns of a warpgroup (128 from column 128 * wg):
+//   D [0, 64)    FP32 accumulator, shared by layer 1 and layer 2
+//   X [64, 96)   layer-1 input: [f or f' (32 bf16) | PE(w) (27) | 1 | 1 | 0 ...]
+//   H [96, 128)  layer-2 input: bf16(ReLU(layer 1))
+// Column c of X or H holds the bf16 pair (2c, 2c + 1) of the row.
+constexpr int TM_D = 0, TM_X = 64, TM_H = 96;
 constexpr int kPixSlots = 34;                // pixels touched by one tile when N >= 4
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int SM_W = 0;
-constexpr int WG_X = 0;                      // A tile [128][64] bf16, swizzled
-constexpr int WG_H = 16384;                  // hidden activations [128][64] bf16, swizzled
-constexpr int WG_FPIX = 32768;               // primary features [34][32] bf16; reused as red[128] float4
-constexpr int WG_MISC = WG_FPIX + 2560;      // mbarrier (8), then carry[NL] float4 from +16
-constexpr int WG_BYTES = 35840;
+constexpr int WG_FPIX = 0;                   // primary features [34][32] bf16; reused as red[128] float4
+constexpr int WG_MISC = 2560;                // mbarrier (8), then carry[NL] float4 from +16
+constexpr int WG_BYTES = 2816;
 constexpr int SM_WG = WBF16_BYTES;
 static_assert(WG_MISC + 16 + 8 * 16 <= WG_BYTES, "warpgroup block overflow");
 static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
@@ -153,6 +160,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+// The same with the A operand in tensor memory (rows in lanes, K-major bf16 pairs).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -215,6 +231,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
@@ -227,43 +257,35 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
-__device__ __forceinline__ void st_chunk(uint8_t* tile, int row, int chunk, uint32_t a, uint32_t b, uint32_t c,
-                                         uint32_t d) {
-  *reinterpret_cast<uint4*>(tile + row * 128 + ((chunk ^ (row & 7)) << 4)) = make_uint4(a, b, c, d);
-}
-
-// D <- A[128 x 16*ksteps] . B[N x 16*ksteps]^T
-__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a_s, uint32_t b_s, int ksteps, uint32_t idesc) {
-  for (int k = 0; k < ksteps; ++k) mma_bf16(d, sdesc(a_s + 32 * k), sdesc(b_s + 32 * k), idesc, k > 0 ? 1u : 0u);
+// D <- X . W1^T (k-steps 0..3 of the layer-1 input in TMEM)
+__device__ __forceinline__ void mma_layer1(uint32_t d, uint32_t x_t, uint32_t w_s) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mma_bf16_ts(d, x_t + 8 * k, sdesc(w_s + 32 * k), kIdescN64, k > 0 ? 1u : 0u);
 }
 // layer 2: D <- H . W2^T + ones . Bias2^T
-__device__ __forceinline__ void mma_layer2(uint32_t d, uint32_t h_s, uint32_t w_s, uint32_t ones_s, uint32_t bias_s) {
-  mma_chain(d, h_s, w_s, 4, kIdescN64);
+__device__ __forceinline__ void mma_layer2(uint32_t d, uint32_t h_t, uint32_t w_s, uint32_t ones_s, uint32_t bias_s) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mma_bf16_ts(d, h_t + 8 * k, sdesc(w_s + 32 * k), kIdescN64, k > 0 ? 1u : 0u);
   mma_bf16(d, sdesc32(ones_s), sdesc32(bias_s), kIdescN64, 1u);
 }
 // B's layer 1: f' (k-steps 0, 1) and the bias columns (k-step 3; B's weights are zero on the PE columns)
-__device__ __forceinline__ void mma_brdf_layer1(uint32_t d, uint32_t x_s, uint32_t w_s) {
-  mma_bf16(d, sdesc(x_s), sdesc(w_s), kIdescN64, 0u);
-  mma_bf16(d, sdesc(x_s + 32), sdesc(w_s + 32), kIdescN64, 1u);
-  mma_bf16(d, sdesc(x_s + 96), sdesc(w_s + 96), kIdescN64, 1u);
+__device__ __forceinline__ void mma_brdf_layer1(uint32_t d, uint32_t x_t, uint32_t w_s) {
+  mma_bf16_ts(d, x_t, sdesc(w_s), kIdescN64, 0u);
+  mma_bf16_ts(d, x_t + 8, sdesc(w_s + 32), kIdescN64, 1u);
+  mma_bf16_ts(d, x_t + 24, sdesc(w_s + 96), kIdescN64, 1u);
 }
 
 // hidden epilogue: H[row] = bf16(relu(D[row][0:64])) (the bias is already in D)
-__device__ __forceinline__ void epilogue_hidden(uint32_t taddr, uint8_t* H, int row) {
+__device__ __forceinline__ void epilogue_hidden(uint32_t d_taddr, uint32_t h_taddr) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t r[32];
-    tmem_ld32(taddr + 32 * h, r);
+    tmem_ld32(d_taddr + 32 * h, r);
     tmem_ld_wait();
+    uint32_t q[16];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      uint32_t q[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        q[e] = pack_relu_bf16(__uint_as_float(r[8 * c + 2 * e]), __uint_as_float(r[8 * c + 2 * e + 1]));
-      }
-      st_chunk(H, row, 4 * h + c, q[0], q[1], q[2], q[3]);
-    }
+    for (int e = 0; e < 16; ++e) q[e] = pack_relu_bf16(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
+    tmem_st16(h_taddr + 16 * h, q);
   }
 }
 
@@ -287,75 +309,83 @@ __device__ __forceinline__ void head_fp32(uint32_t taddr, const float* W3, const
 }
 
 
-// f' = H(x') as 16 packed bf16 pairs (zero beyond L levels), from an FP16
-// table.  The two x-neighbour corners of a cell share one 8-byte load when
-// their rows form an aligned pair (rows r and r ^ 1: a hashed level with even
-// i, or a dense level with an even row), which removes about a quarter of
-// the gathers.  The loads of kEncBatch levels are issued before any is used.
-constexpr int kEncBatch = 2;
-__device__ __forceinline__ void encode_point_bf16(const GridDesc& g, f3 x, uint32_t (&fq)[16]) {
+// f' = H(x') as 16 bf16 pairs written to X columns 0..15 (zero beyond L
+// levels), from an FP16 table.  The loop over groups of four levels stays
+// rolled (the unrolled sixteen levels cost more in instruction fetch than
+// they save); within a group the loads of two levels are issued before any
+// is used.  The two x-neighbour corners of a cell share one 8-byte load when
+// their rows form an aligned pair (rows r and r ^ 1: a hashed level with
+// even i, or a dense level with an even row), which removes about a quarter
+// of the gathers.
+__device__ __forceinline__ void encode_point_tmem(const GridDesc& g, f3 x, uint32_t x_taddr) {
+#pragma unroll 1
+  for (int it = 0; it < kMaxLevels / 4; ++it) {
+    uint32_t fq[4];
 #pragma unroll
-  for (int l0 = 0; l0 < kMaxLevels; l0 += kEncBatch) {
-    uint32_t v[kEncBatch][8];
-    float w[kEncBatch][3];
+    for (int sb = 0; sb < 2; ++sb) {
+      uint32_t v[2][8];
+      float w[2][3];
 #pragma unroll
-    for (int b = 0; b < kEncBatch; ++b) {
-      const int l = l0 + b;
-      if (l < g.levels) {
-        const int res = g.res[l];
-        uint32_t ix, iy, iz;
-        grid_cell(x.x, res, ix, w[b][0]);
-        grid_cell(x.y, res, iy, w[b][1]);
-        grid_cell(x.z, res, iz, w[b][2]);
-        const uint32_t* tab = reinterpret_cast<const uint32_t*>(g.table) + ((size_t)l << g.log2T);
+      for (int b = 0; b < 2; ++b) {
+        const int l = 4 * it + 2 * sb + b;
+        if (l < g.levels) {
+          const int res = g.res[l];
+          uint32_t ix, iy, iz;
+          grid_cell(x.x, res, ix, w[b][0]);
+          grid_cell(x.y, res, iy, w[b][1]);
+          grid_cell(x.z, res, iz, w[b][2]);
+          const uint32_t* tab = reinterpret_cast<const uint32_t*>(g.table) + ((size_t)l << g.log2T);
+          const int dn = g.dense[l];
 #pragma unroll
-        for (int yz = 0; yz < 4; ++yz) {
-          const uint32_t r0 = corner_row(ix, iy + (yz & 1), iz + (yz >> 1), res, g.dense[l], g.mask);
-          const uint32_t r1 = corner_row(ix + 1, iy + (yz & 1), iz + (yz >> 1), res, g.dense[l], g.mask);
-          const uint2 pr = __ldg(reinterpret_cast<const uint2*>(tab + (r0 & ~1u)));
-          const bool odd = r0 & 1u;
-          v[b][2 * yz] = odd ? pr.y : pr.x;
-          v[b][2 * yz + 1] = ((r0 ^ r1) == 1u) ? (odd ? pr.x : pr.y) : __ldg(tab + r1);
+          for (int yz = 0; yz < 4; ++yz) {
+            const uint32_t r0 = corner_row(ix, iy + (yz & 1), iz + (yz >> 1), res, dn, g.mask);
+            const uint32_t r1 = corner_row(ix + 1, iy + (yz & 1), iz + (yz >> 1), res, dn, g.mask);
+            const uint2 pr = __ldg(reinterpret_cast<const uint2*>(tab + (r0 & ~1u)));
+            const bool odd = r0 & 1u;
+            v[b][2 * yz] = odd ? pr.y : pr.x;
+            v[b][2 * yz + 1] = ((r0 ^ r1) == 1u) ? (odd ? pr.x : pr.y) : __ldg(tab + r1);
+          }
         }
       }
-    }
 #pragma unroll
-    for (int b = 0; b < kEncBatch; ++b) {
-      const int l = l0 + b;
-      float f0 = 0.f, f1 = 0.f;
-      if (l < g.levels) {
+      for (int b = 0; b < 2; ++b) {
+        const int l = 4 * it + 2 * sb + b;
+        float f0 = 0.f, f1 = 0.f;
+        if (l < g.levels) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          // v[b][2*yz + dx] holds corner (dx, yz & 1, yz >> 1)
-          const int dx = c & 1, yz = c >> 1;
-          const float wt = (dx ? w[b][0] : 1.0f - w[b][0]) * ((yz & 1) ? w[b][1] : 1.0f - w[b][1]) *
-                           ((yz & 2) ? w[b][2] : 1.0f - w[b][2]);
-          const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[b][c]));
-          f0 = fmaf(wt, e.x, f0);
-          f1 = fmaf(wt, e.y, f1);
+          for (int c = 0; c < 8; ++c) {
+            // v[b][2*yz + dx] holds corner (dx, yz & 1, yz >> 1)
+            const int dx = c & 1, yz = c >> 1;
+            const float wt = (dx ? w[b][0] : 1.0f - w[b][0]) * ((yz & 1) ? w[b][1] : 1.0f - w[b][1]) *
+                             ((yz & 2) ? w[b][2] : 1.0f - w[b][2]);
+            const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[b][c]));
+            f0 = fmaf(wt, e.x, f0);
+            f1 = fmaf(wt, e.y, f1);
+          }
         }
+        fq[2 * sb + b] = pack_bf16(f0, f1);
       }
-      fq[l] = pack_bf16(f0, f1);
     }
+    tmem_st4(x_taddr + 4 * it, fq[0], fq[1], fq[2], fq[3]);
   }
 }
 
-// PE(w) as bf16 into chunks 4..7 of the A tile row: 27 values, then the two
-// 1.0 columns that carry layer 1's bias, then zeros
-__device__ __forceinline__ void store_pe_bf16(uint8_t* X, int row, f3 w) {
+// PE(w) as bf16 into X columns 16..31: 27 values, then the two 1.0 columns
+// that carry layer 1's bias, then zeros
+__device__ __forceinline__ void store_pe_tmem(uint32_t x_taddr, f3 w) {
   float pe[32];
   positional_encoding_fast(w, [&](int k, float v) { pe[k] = v; });
 #pragma unroll
   for (int k = kPE; k < 32; ++k) pe[k] = (k == kBiasCol - 32 || k == kBiasCol - 31) ? 1.0f : 0.0f;
+  uint32_t q[16];
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
-    st_chunk(X, row, 4 + c, pack_bf16(pe[8 * c], pe[8 * c + 1]), pack_bf16(pe[8 * c + 2], pe[8 * c + 3]),
-             pack_bf16(pe[8 * c + 4], pe[8 * c + 5]), pack_bf16(pe[8 * c + 6], pe[8 * c + 7]));
+  for (int e = 0; e < 16; ++e) q[e] = pack_bf16(pe[2 * e], pe[2 * e + 1]);
+  tmem_st16(x_taddr + 16, q);
 }
 
 template <int NL, int WG>
 __global__ void __launch_bounds__(Layout<WG>::kThreads, Layout<WG>::kMinBlocks)
-render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P, long long pixel_offset,
+render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P, long long pixel_offset,
                    const float4* __restrict__ envs, float4* __restrict__ out) {
   constexpr int kThreadsB = Layout<WG>::kThreads;
   extern __shared__ uint8_t smem_raw[];
@@ -364,8 +394,6 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   const int wg = tid >> 7, t = tid & 127, warp = t >> 5, lane = t & 31;
   uint8_t* Wsm = sm + SM_W;
   uint8_t* wgb = sm + SM_WG + wg * WG_BYTES;
-  uint8_t* X = wgb + WG_X;
-  uint8_t* H = wgb + WG_H;
   uint8_t* fpix = wgb + WG_FPIX;
   float4* red = reinterpret_cast<float4*>(wgb + WG_FPIX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WG_MISC);
@@ -379,7 +407,7 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
     mbar_init(smem_u32(bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  fence_async_smem();
+  fence_async_smem();   // the weight tiles are read by the async proxy
   if (warp == 0 && wg == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(Layout<WG>::kTmemCols)
@@ -390,10 +418,11 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot + (uint32_t)(128 * wg);
-  const uint32_t D1 = tmem, D2 = tmem + 64;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+  const uint32_t D_t = tmem + TM_D, X_t = tmem + TM_X, H_t = tmem + TM_H;   // MMA operands (lane 0)
+  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;                    // this warp's 32 lanes
+  const uint32_t D_w = D_t + lane_off, X_w = X_t + lane_off, H_w = H_t + lane_off;
   const uint32_t bar_a = smem_u32(bar);
-  const uint32_t X_s = smem_u32(X), H_s = smem_u32(H), W_s = smem_u32(Wsm);
+  const uint32_t W_s = smem_u32(Wsm);
 
   const int N = m.N, M = m.M;
   const int env_hw = m.env_h * m.env_w;
@@ -416,7 +445,7 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
   // warpgroup never splits across barriers.
   uint32_t pending_phase = 0;
   auto run_mma = [&](auto issue) -> bool {
-    fence_async_smem();
+    tmem_st_wait();   // this thread's rows of the A operand have landed in TMEM
     tc_fence_before();
     abort = wg_sync_or(wg, abort);
     if (abort) return false;
@@ -492,22 +521,27 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
     if (NL == 1) le1 = env_fetch(envs, tap1);
     {
       const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
+      uint32_t fr[16];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const uint4 v = src[c];
-        st_chunk(X, t, c, v.x, v.y, v.z, v.w);
+        fr[4 * c] = v.x;
+        fr[4 * c + 1] = v.y;
+        fr[4 * c + 2] = v.z;
+        fr[4 * c + 3] = v.w;
       }
+      tmem_st16(X_w, fr);
     }
-    store_pe_bf16(X, t, wi);
+    store_pe_tmem(X_w, wi);
 
     // (c) I(f, w_i)
-    if (!run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); })) break;
-    epilogue_hidden(D1 + lane_off, H, t);
-    if (!run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
+    if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) break;
+    epilogue_hidden(D_w, H_w);
+    if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
     float v, tdep;
     {
       float z[2];
-      head_fp32<2, 2>(D2 + lane_off, &hp.iw3[0][0], hp.ib3, z);
+      head_fp32<2, 2>(D_w, &hp.iw3[0][0], hp.ib3, z);
       v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
       tdep = depth_fast(z[1], m.near_t, m.far_t);
     }
@@ -524,24 +558,18 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       }
     }
 
-    // (d) bounce: x' = x + t w_i; f' = H(x') into chunks 0..3 of the A tile
-    {
-      const f3 x2 = x + wi * tdep;
-      uint32_t fq[16];
-      encode_point_bf16(m.grid, x2, fq);
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) st_chunk(X, t, cc, fq[4 * cc], fq[4 * cc + 1], fq[4 * cc + 2], fq[4 * cc + 3]);
-    }
+    // (d) bounce: x' = x + t w_i; f' = H(x') into X columns 0..15
+    encode_point_tmem(m.grid, x + wi * tdep, X_w);
 
     // (b) B(f')
-    if (!run_mma([&] { mma_brdf_layer1(D1, X_s, W_s + OFFB_BW1); })) break;
-    epilogue_hidden(D1 + lane_off, H, t);
-    if (!run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) break;
+    if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) break;
+    epilogue_hidden(D_w, H_w);
+    if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) break;
     f3 n2, a2;
     float r2;
     {
       float y[7];
-      head_fp32<7, 8>(D2 + lane_off, &hp.bw3[0][0], hp.bb3, y);
+      head_fp32<7, 8>(D_w, &hp.bw3[0][0], hp.bb3, y);
       const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
       n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
       a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
@@ -558,14 +586,14 @@ render_bf16_kernel(ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffe
       const f3 frw = fr1 * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
       f3 lej = mk(0.f, 0.f, 0.f);
       if (NL == 1) lej = env_fetch(envs, tapj);
-      store_pe_bf16(X, t, wj);
-      ok = run_mma([&] { mma_chain(D1, X_s, W_s + OFFB_IW1, 4, kIdescN64); });
+      store_pe_tmem(X_w, wj);
+      ok = run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); });
       if (!ok) break;
-      epilogue_hidden(D1 + lane_off, H, t);
-      ok = run_mma([&] { mma_layer2(D2, H_s, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
+      epilogue_hidden(D_w, H_w);
+      ok = run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
       if (!ok) break;
       float z0[1];
-      head_fp32<1, 2>(D2 + lane_off, &hp.iw3[0][0], hp.ib3, z0);
+      head_fp32<1, 2>(D_w, &hp.iw3[0][0], hp.ib3, z0);
       const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(z0[0]);
       const f3 wj3 = frw * (wsec * v2);
       if (NL == 1) {
