@@ -205,7 +205,7 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
  * bounce): each row contributes fr1 (v Lenv(w_i) + (1 - v) (pi/M) sum_j v'_j
  * fr2_j Lenv(w'_j)) to every light.  Lights per launch (1, 2, 4, 8) and
  * warpgroups per CTA (2: two CTAs per SM; 3 or 4: one CTA per SM) follow the
- * context's launch shape (rt_tune / rt_set_launch_shape; default 8 and 3),
+ * context's launch shape (rt_tune / rt_set_launch_shape; default 8 and 4),
  * which rt_render_frame (one light) also uses.  The FP32 path renders one light
  * per pass.  Equal, light by light, to rt_render_frame with that map bound.
  * E in 0..1024.  No allocation, no synchronisation: capturable. */

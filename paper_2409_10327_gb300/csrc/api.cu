@@ -20,10 +20,10 @@ struct rt_ctx {
   uint32_t* status;    // device status word
   const void* table;
   const float* env;
-  HeadParams head;     // host copy of the FP32 biases / output layers (BF16 kernel parameter)
+  HeadParams head;     // host copy of the FP32 output layers (BF16 kernel parameter)
   bool ready;
   int tuned_nl;        // lights per launch of the BF16 kernel (rt_tune), default 8
-  int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 3
+  int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 4
 };
 
 namespace {
@@ -182,7 +182,7 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
   if (ctx == nullptr) return RT_ERR_OOM;
   ctx->cfg = *cfg;
   ctx->tuned_nl = 8;
-  ctx->tuned_wg = 3;
+  ctx->tuned_wg = 4;
   for (int l = 0; l < cfg->levels; ++l) {
     ctx->res[l] = level_res(cfg, l);
     ctx->dense[l] = level_dense(cfg, ctx->res[l]) ? 1 : 0;
@@ -243,19 +243,16 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
   rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, s));
   if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, s));
   if (st != RT_OK) return st;
-  // host copy of the biases and output layers for the BF16 kernel's parameters
+  // host copy of the output layers for the BF16 kernel's parameters
   static thread_local float host[WPACK_FLOATS];
   if (cudaMemcpyAsync(host, ctx->wpack, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return RT_ERR_CUDA;
   HeadParams& h = ctx->head;
   for (int i = 0; i < 64; ++i) {
-    h.ib1[i] = host[OFF_IB1 + i];
-    h.ib2[i] = host[OFF_IB2 + i];
-    h.bb1[i] = host[OFF_BB1 + i];
-    h.bb2[i] = host[OFF_BB2 + i];
     h.iw3[i][0] = host[OFF_IW3 + 2 * i];
     h.iw3[i][1] = host[OFF_IW3 + 2 * i + 1];
+    h.iw3v[i] = host[OFF_IW3 + 2 * i];
     for (int o = 0; o < 8; ++o) h.bw3[i][o] = host[OFF_BW3 + 8 * i + o];
   }
   h.ib3[0] = host[OFF_IB3];

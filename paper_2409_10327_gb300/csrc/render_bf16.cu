@@ -289,11 +289,13 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t d_taddr, uint32_t h_tad
   }
 }
 
-// Output layer in FP32: z[o] = b3[o] + sum_k relu(D[row][k]) W3[k][o] (b2 is already in D)
+// Output layer in FP32 with packed FMAs: z[o] = b3[o] + sum_k relu(D[row][k]) W3[k][o]
 template <int NOUT, int LDW>
 __device__ __forceinline__ void head_fp32(uint32_t taddr, const float* W3, const float* b3, float (&z)[NOUT]) {
+  constexpr int NP = (NOUT + 1) / 2;
+  float2 acc[NP];
 #pragma unroll
-  for (int o = 0; o < NOUT; ++o) z[o] = b3[o];
+  for (int o = 0; o < NP; ++o) acc[o] = make_float2(b3[2 * o], 2 * o + 1 < NOUT ? b3[2 * o + 1] : 0.0f);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t r[32];
@@ -302,10 +304,31 @@ __device__ __forceinline__ void head_fp32(uint32_t taddr, const float* W3, const
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
       const float a = fmaxf(__uint_as_float(r[k]), 0.0f);
+      const float2 aa = make_float2(a, a);
 #pragma unroll
-      for (int o = 0; o < NOUT; ++o) z[o] = fmaf(a, W3[(32 * h + k) * LDW + o], z[o]);
+      for (int o = 0; o < NP; ++o)
+        acc[o] = __ffma2_rn(aa, *reinterpret_cast<const float2*>(&W3[(32 * h + k) * LDW + 2 * o]), acc[o]);
     }
   }
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) z[o] = (o & 1) ? acc[o / 2].y : acc[o / 2].x;
+}
+
+// One output (I's visibility logit): pairs of hidden units per packed FMA.
+__device__ __forceinline__ float head_vis(uint32_t taddr, const float* w, float b) {
+  float2 acc = make_float2(b, 0.0f);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t r[32];
+    tmem_ld32(taddr + 32 * h, r);
+    tmem_ld_wait();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float2 a = make_float2(fmaxf(__uint_as_float(r[2 * k]), 0.0f), fmaxf(__uint_as_float(r[2 * k + 1]), 0.0f));
+      acc = __ffma2_rn(a, *reinterpret_cast<const float2*>(&w[32 * h + 2 * k]), acc);
+    }
+  }
+  return acc.x + acc.y;
 }
 
 
@@ -592,9 +615,7 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
       epilogue_hidden(D_w, H_w);
       ok = run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
       if (!ok) break;
-      float z0[1];
-      head_fp32<1, 2>(D_w, &hp.iw3[0][0], hp.ib3, z0);
-      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(z0[0]);
+      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(head_vis(D_w, hp.iw3v, hp.ib3[0]));
       const f3 wj3 = frw * (wsec * v2);
       if (NL == 1) {
         c[0] = c[0] + wj3 * lej;
@@ -732,7 +753,7 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 
 cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                long long offset, float4* out, int num_sms, cudaStream_t s) {
-  return launch_variant<1, 3>(m, hp, gb, P, offset, m.env, out, num_sms, s);
+  return launch_variant<1, 4>(m, hp, gb, P, offset, m.env, out, num_sms, s);
 }
 
 }  // namespace rtk

@@ -91,13 +91,17 @@ struct ModelDesc {
 
 // FP32 biases and output layers of both MLPs, passed to the BF16 kernel by
 // value as a kernel parameter (constant bank) so that its epilogues read them
-// without shared-memory traffic.  Filled on the host by rt_set_params.
-struct HeadParams {
-  float ib1[64], ib2[64], ib3[2];
-  float bb1[64], bb2[64], bb3[8];
-  float iw3[64][2];
-  float bw3[64][8];
+// without shared-memory traffic.  Filled on the host by rt_set_params.  The
+// output layers are read as float2 pairs, hence the 8-byte alignment.
+struct alignas(16) HeadParams {
+  float ib3[2], bb3[8];
+  float iw3[64][2];             // I's output layer, [hidden][output]
+  float bw3[64][8];             // B's output layer, [hidden][output] (column 7 zero)
+  float iw3v[64];               // I's visibility row, contiguous
 };
+static_assert(offsetof(HeadParams, iw3) % 8 == 0 && offsetof(HeadParams, bw3) % 8 == 0 &&
+                  offsetof(HeadParams, iw3v) % 8 == 0,
+              "float2 reads of the output layers");
 
 // Launch helpers implemented in the .cu files.
 // One-time per-device kernel attributes (large dynamic shared memory); called by rt_create.
