@@ -196,6 +196,41 @@ def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
     return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev], clk
 
 
+# Per-launch DRAM traffic of the timed kernels, from one ncu pass over a whole
+# frame (dram__bytes_read.sum + dram__bytes_write.sum).  Each record names the
+# SHA-256 of the kernel's sources at capture time; a kernel changed since then
+# reports null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_frame800.txt")
+KERNEL_SOURCES = {
+    "bf16": ["render_bf16.cu", "fast_math.cuh", "device_common.cuh", "rt_internal.h"],
+    "fp32": ["render_fp32.cu", "warp_gemm.cuh", "device_common.cuh", "rt_internal.h"],
+}
+
+
+def kernel_source_hash(precision: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[precision]:
+        with open(os.path.join(ROOT, "paper_2409_10327_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(cfg):
+    """DRAM bytes per launch for this precision at the 800x800 workload, or None."""
+    if cfg.n_pixels != 800 * 800 or not os.path.exists(TRAFFIC_FILE):
+        return None
+    want = kernel_source_hash(cfg.precision)
+    with open(TRAFFIC_FILE) as fh:
+        for line in fh:
+            if line.startswith("#") or "=" not in line:
+                continue
+            kv = dict(item.split("=", 1) for item in line.split())
+            if kv.get("precision") == cfg.precision and kv.get("source_sha256") == want:
+                return int(kv["bytes_per_launch"])
+    return None
+
+
 def _roofline(cfg, launch_ms, peaks):
     flop = algorithmic_flop_per_sample(cfg) * cfg.samples
     avg_s = sum(launch_ms) / len(launch_ms) / 1e3
@@ -207,7 +242,7 @@ def _roofline(cfg, launch_ms, peaks):
         roof = {"bound": "tensor", "achieved": flop / avg_s / 1e12, "peak": pk if pk else 1700.0, "unit": "TFLOP/s",
                 "peak_source": "of measured (bf16_tflops_sustained)" if pk else "of fallback"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(cfg)
     roof["algorithmic_per_launch"] = flop
     roof["kernel_ms"] = avg_s * 1e3
     gather_bytes = cfg.samples * cfg.levels * 8 * (4 if cfg.precision == "bf16" else 8)
