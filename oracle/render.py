@@ -18,9 +18,12 @@ overview):
           L(x, w_i) = v_i L_env(w_i) + (1 - v_i) L'_o,i                 (Eq. 2)
   (e) L(x, w_o) = (pi/N) sum_i L(x, w_i) f_r(a, r, n; w_i, w_o)          (Eq. 1)
 
-Readings (the paper's inference uses hard visibility and only bounces
-shadow rays, Sec. 3.2): the default is the soft, differentiable form of
-Eq. 2 in which every direction bounces with weight (1 - v);  `force_vis`
+Readings: the default is the soft, differentiable form of Eq. 2 in which
+every direction bounces with weight (1 - v).  `hard_vis` is the paper's
+inference (Sec. 3.2 overview): I's visibility is a hit test, v = 1 when
+sigma(z0) > 0.5 and 0 otherwise, for v and v' alike, so only shadow
+directions (v = 0) bounce and only visible secondary directions (v' = 1)
+count at x'; Eq. 2 is unchanged with V in {0, 1}.  `force_vis`
 and `force_vis2` pin v or v' to a constant (used by the furnace tests);
 `lambert` drops the specular lobe.  There is no third bounce: the secondary
 sum keeps only the environment light that reaches x' (v'), as in the
@@ -58,6 +61,7 @@ class Options:
     lambert: bool = False
     force_vis: float = -1.0      # < 0: use I's visibility
     force_vis2: float = -1.0
+    hard_vis: bool = False       # v, v' = 1[sigma(z0) > 0.5] (Sec. 3.2 overview)
     dir_seed: int = 0x5EED
     dense_coarse: bool = True
     # conditioning probe: relative Gaussian jitter of the secondary points x'
@@ -124,6 +128,8 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
     v, t = mlp.implicit_ray_tracer(f_rep, w_i.reshape(P * N, 3), prm.irt, opt.near, opt.far, jit)
+    if opt.hard_vis:
+        v = (v > 0.5).to(v.dtype)
     if opt.force_vis >= 0:
         v = torch.full_like(v, opt.force_vis)
 
@@ -145,6 +151,8 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     f2_rep = f2[:, None, :].expand(P * N, M, f2.shape[1]).reshape(P * N * M, -1)
     v2, _ = mlp.implicit_ray_tracer(f2_rep, w_j.reshape(-1, 3), prm.irt, opt.near, opt.far, jit)
     v2 = v2.reshape(P * N, M)
+    if opt.hard_vis:
+        v2 = (v2 > 0.5).to(v2.dtype)
     if opt.force_vis2 >= 0:
         v2 = torch.full_like(v2, opt.force_vis2)
 

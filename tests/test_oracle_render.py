@@ -165,3 +165,47 @@ def test_gradient_matches_central_differences():
             assert abs(float(g[idx]) - fds[2]) <= tol, (leaf.shape, idx, float(g[idx]), fds)
             checked += 1
     assert checked >= 30
+
+
+# ---- hard visibility (the paper's inference, Sec. 3.2 overview) -------------
+
+def _scaled_visibility_row(prm, scale=None, const=None):
+    """Copy of prm with I's output row 0 (the visibility logit z0) scaled, or set to a constant."""
+    (w1, b1), (w2, b2), (w3, b3) = prm.irt
+    w3, b3 = w3.clone(), b3.clone()
+    if scale is not None:
+        w3[0] *= scale
+        b3[0] *= scale
+    if const is not None:
+        w3[0] = 0.0
+        b3[0] = const
+    return dataclasses.replace(prm, irt=[(w1, b1), (w2, b2), (w3, b3)])
+
+
+def test_hard_visibility_ignores_a_positive_scale_of_the_logit():
+    # v = 1[sigmoid(z0) > 0.5] depends on the sign of z0 only; the soft blend does not
+    gb, prm = _setup(bias=0.2)
+    prm7 = _scaled_visibility_row(prm, scale=7.5)
+    hard, hard7 = (render.render(gb, p, _opt(hard_vis=True)) for p in (prm, prm7))
+    np.testing.assert_array_equal(hard, hard7)
+    soft, soft7 = (render.render(gb, p, _opt()) for p in (prm, prm7))
+    assert np.max(np.abs(soft - soft7)) > 1e-3
+
+
+def test_hard_visibility_is_the_saturated_sigmoid():
+    # the soft path with z0 scaled by 1e9 has sigmoid(z0) in {0, 1} exactly in float64, for v and v'
+    gb, prm = _setup(bias=0.2)
+    hard = render.render(gb, prm, _opt(hard_vis=True))
+    soft_sat = render.render(gb, _scaled_visibility_row(prm, scale=1e9), _opt())
+    np.testing.assert_allclose(hard, soft_sat, rtol=1e-12, atol=1e-15)
+    assert np.max(np.abs(hard - render.render(gb, prm, _opt()))) > 1e-3
+
+
+@pytest.mark.parametrize("z0, forced", [(0.5, dict(force_vis=1.0)), (-0.5, dict(force_vis=0.0, force_vis2=0.0))])
+def test_hard_visibility_with_a_constant_logit(z0, forced):
+    # z0 > 0 everywhere: every direction is visible, nothing bounces (the direct term alone);
+    # z0 < 0 everywhere: every direction is a shadow ray whose secondary directions are all occluded
+    gb, prm = _setup(bias=0.2)
+    hard = render.render(gb, _scaled_visibility_row(prm, const=z0), _opt(hard_vis=True))
+    ref = render.render(gb, prm, _opt(**forced))
+    np.testing.assert_allclose(hard, ref, rtol=1e-13, atol=0)
