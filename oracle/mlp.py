@@ -20,6 +20,17 @@ Pins (tests/test_oracle_mlp.py): the MLP against a numpy float64 matmul
 chain; sigmoid/softplus at known points; the positional encoding against
 its closed-form values at w = 0 and at the axes; the depth mapping at its
 end points.
+
+Kernel arithmetic (`mlp3_arith`), used only where floating point decides an
+integer: the hard-visibility hit test 1[z0 > 0] of the paper's inference is
+taken on the logit as a kernel computes it.  'bf16' rounds the layer
+inputs, the two hidden weight matrices and the first hidden activations to
+bfloat16 (round to nearest even) and keeps the biases and the output layer
+in float32, with float64 sums (the tensor cores' float32 accumulation
+differs from them only in summation order); 'fp32' rounds every operand and
+every layer result to float32.  Pins: exact agreement with `mlp3` when all
+roundings are exact, and the rounding of each stage observed on values that
+are not representable (tests/test_oracle_mlp.py).
 """
 from __future__ import annotations
 
@@ -59,6 +70,29 @@ def mlp3(z: torch.Tensor, layers: Layers, jitter=None) -> torch.Tensor:
     h1 = torch.relu(_jit(z, jitter) @ w1.T + b1)
     h2 = torch.relu(_jit(h1, jitter) @ w2.T + b2)
     return _jit(h2, jitter) @ w3.T + b3
+
+
+def round_to(x: torch.Tensor, arith: str) -> torch.Tensor:
+    """x rounded to a narrower IEEE format (round to nearest even), returned in float64."""
+    dt = {"bf16": torch.bfloat16, "fp16": torch.float16, "fp32": torch.float32}[arith]
+    return x.to(dt).to(torch.float64)
+
+
+def mlp3_arith(z: torch.Tensor, layers: Layers, arith: str) -> torch.Tensor:
+    """mlp3 in a kernel's arithmetic ('bf16' or 'fp32'; see the module notes)."""
+    (w1, b1), (w2, b2), (w3, b3) = layers
+    if arith == "bf16":
+        r16 = lambda a: round_to(a, "bf16")
+        r32 = lambda a: round_to(a, "fp32")
+        h1 = r32(torch.relu(r16(z) @ r16(w1).T + r32(b1)))
+        h2 = r32(torch.relu(r16(h1) @ r16(w2).T + r32(b2)))
+        return r32(h2 @ r32(w3).T + r32(b3))
+    if arith == "fp32":
+        f = lambda a: a.to(torch.float32)
+        h1 = torch.relu(f(z) @ f(w1).T + f(b1))
+        h2 = torch.relu(h1 @ f(w2).T + f(b2))
+        return (h2 @ f(w3).T + f(b3)).to(torch.float64)
+    raise ValueError(arith)
 
 
 def brdf_decoder(f: torch.Tensor, layers: Layers, jitter=None):

@@ -23,7 +23,13 @@ every direction bounces with weight (1 - v).  `hard_vis` is the paper's
 inference (Sec. 3.2 overview): I's visibility is a hit test, v = 1 when
 sigma(z0) > 0.5 and 0 otherwise, for v and v' alike, so only shadow
 directions (v = 0) bounce and only visible secondary directions (v' = 1)
-count at x'; Eq. 2 is unchanged with V in {0, 1}.  `force_vis`
+count at x'; Eq. 2 is unchanged with V in {0, 1}.  The hit test decides an
+integer from floating point, so it is taken in the arithmetic of the kernel
+under test (`decision_arith`: 'fp64', 'fp32' or 'bf16'; see
+`_kernel_logits`); the radiance given those decisions stays float64.
+`flip_margin` > 0 also returns, per pixel, what flipping the decision of
+every row whose logit lies within that margin of 0 could change (the rows a
+kernel may decide the other way through its own rounding).  `force_vis`
 and `force_vis2` pin v or v' to a constant (used by the furnace tests);
 `lambert` drops the specular lobe.  There is no third bounce: the secondary
 sum keeps only the environment light that reaches x' (v'), as in the
@@ -62,6 +68,8 @@ class Options:
     force_vis: float = -1.0      # < 0: use I's visibility
     force_vis2: float = -1.0
     hard_vis: bool = False       # v, v' = 1[sigma(z0) > 0.5] (Sec. 3.2 overview)
+    decision_arith: str = "fp64"  # arithmetic of the hard decisions: 'fp64', 'fp32' or 'bf16'
+    flip_margin: float = 0.0     # > 0: also return the flip allowance of rows with |z0| < margin
     dir_seed: int = 0x5EED
     dense_coarse: bool = True
     # conditioning probe: relative Gaussian jitter of the secondary points x'
@@ -106,9 +114,47 @@ def _gbuffer_tensors(gb: Dict[str, np.ndarray], rows: np.ndarray):
     return g("pos", 3), g("normal", 3), g("view", 3), ar[:, :3], ar[:, 3]
 
 
+def _kernel_logits(x, n, q, prm: Params, opt: Options, res, dense):
+    """Visibility logits z0 [P, N] and z0' [P*N, M] as a kernel computes them.
+
+    The chain that leads to the decisions (f, I, the bounce, f', B, the
+    secondary directions, I again) is re-evaluated in opt.decision_arith:
+    the table as the kernel reads it (FP16 for 'bf16'), the cell decision of
+    the hash grid in float32, the features rounded to the MLP input format,
+    and the MLPs in mlp3_arith.  Directions and depth are float64.
+    """
+    arith = opt.decision_arith
+    P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
+    w_i = sampling.cosine_direction(n[:, None, :], u1, u2)                    # unjittered, [P, N, 3]
+    tab = mlp.round_to(prm.table, "fp16" if arith == "bf16" else "fp32")
+    feat = lambda f: mlp.round_to(f, "bf16" if arith == "bf16" else "fp32")
+    f = feat(hashgrid.encode(x, tab, res, dense, fp32_grid=True))
+    f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
+    y = mlp.mlp3_arith(torch.cat([f_rep, mlp.positional_encoding(w_i.reshape(P * N, 3))], dim=-1), prm.irt, arith)
+    t = mlp.depth_from_logit(torch.nn.functional.softplus(y[:, 1]), opt.near, opt.far)
+    x2 = x[:, None, :] + t.reshape(P, N, 1) * w_i
+    f2 = feat(hashgrid.encode(x2.reshape(P * N, 3), tab, res, dense, fp32_grid=True))
+    yb = mlp.mlp3_arith(f2, prm.brdf, arith)
+    n2 = yb[:, 0:3] / yb[:, 0:3].norm(dim=1, keepdim=True).clamp(min=1e-12)
+    slots = 1 + np.arange(M, dtype=np.uint64)
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q.reshape(-1, 1), slots[None, :], M))
+    w_j = sampling.cosine_direction(n2[:, None, :], u1, u2)
+    f2_rep = f2[:, None, :].expand(P * N, M, f2.shape[1]).reshape(P * N * M, -1)
+    z2 = mlp.mlp3_arith(torch.cat([f2_rep, mlp.positional_encoding(w_j.reshape(-1, 3))], dim=-1), prm.irt, arith)
+    return y[:, 0].reshape(P, N), z2[:, 0].reshape(P * N, M)
+
+
 def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, opt: Options,
-                  fixed_dirs: Optional[torch.Tensor] = None, want_dirs: bool = False):
-    """Radiance [P, 3] of P primary points with global pixel ids (RNG keys)."""
+                  fixed_dirs: Optional[torch.Tensor] = None, want_dirs: bool = False,
+                  decide: Optional[Params] = None):
+    """Radiance [P, 3] of P primary points with global pixel ids (RNG keys).
+
+    decide: the parameters the hard decisions are taken with (default prm);
+    the conditioning probe passes the unperturbed ones so that its jittered
+    renders keep the decisions of the render they are compared with.  With
+    opt.hard_vis and opt.flip_margin > 0 returns (radiance, allowance [P, 3]).
+    """
     P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
     res = hashgrid.level_resolutions(opt.levels, opt.base_res, opt.max_res)
     dense = hashgrid.dense_levels(res, 1 << opt.log2_T, opt.dense_coarse)
@@ -128,8 +174,13 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
     v, t = mlp.implicit_ray_tracer(f_rep, w_i.reshape(P * N, 3), prm.irt, opt.near, opt.far, jit)
+    z0k = z2k = None
     if opt.hard_vis:
-        v = (v > 0.5).to(v.dtype)
+        if opt.decision_arith == "fp64":
+            v = (v > 0.5).to(v.dtype)
+        else:
+            z0k, z2k = _kernel_logits(x, n, q, prm if decide is None else decide, opt, res, dense)
+            v = (z0k.reshape(-1) > 0).to(v.dtype)
     if opt.force_vis >= 0:
         v = torch.full_like(v, opt.force_vis)
 
@@ -152,7 +203,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     v2, _ = mlp.implicit_ray_tracer(f2_rep, w_j.reshape(-1, 3), prm.irt, opt.near, opt.far, jit)
     v2 = v2.reshape(P * N, M)
     if opt.hard_vis:
-        v2 = (v2 > 0.5).to(v2.dtype)
+        v2 = (v2 > 0.5).to(v2.dtype) if z2k is None else (z2k > 0).to(v2.dtype)
     if opt.force_vis2 >= 0:
         v2 = torch.full_like(v2, opt.force_vis2)
 
@@ -164,10 +215,26 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # Eq. 2, then Eq. 1 at x
     v = v.reshape(P, N, 1)
-    li = v * shading.env_lookup(prm.env, w_i) + (1.0 - v) * lo2
+    le1 = shading.env_lookup(prm.env, w_i)
+    li = v * le1 + (1.0 - v) * lo2
     fr1 = shading.brdf(albedo[:, None, :], rough[:, None], n[:, None, :], w_i, wo[:, None, :],
                        opt.f0, opt.lambert)
     out = shading.mc_sum(li * fr1, N)
+    if opt.hard_vis and opt.flip_margin > 0:
+        if z0k is None:
+            raise ValueError("flip_margin needs a kernel decision_arith")
+        amb1 = (z0k.abs() < opt.flip_margin).to(out.dtype)[..., None]                  # [P, N, 1]
+        amb2 = (z2k.abs() < opt.flip_margin).to(out.dtype)[..., None]                  # [P*N, M, 1]
+        if opt.force_vis >= 0:
+            amb1 = torch.zeros_like(amb1)
+        if opt.force_vis2 >= 0:
+            amb2 = torch.zeros_like(amb2)
+        # a flipped v swaps L_env(w_i) and L'_o,i; a flipped v' adds or removes its term of L'_o,i,
+        # which reaches the pixel unless v = 1 is certain
+        d_sec = shading.mc_sum(amb2 * (le2 * fr2).abs(), M).reshape(P, N, 3)
+        reach = torch.maximum(1.0 - v, amb1)
+        allow = shading.mc_sum((amb1 * (le1 - lo2).abs() + reach * d_sec) * fr1.abs(), N)
+        return out, allow
     if want_dirs:
         return out, w_j.detach()
     return out
@@ -186,21 +253,29 @@ def _jitter(opt: Options, global_ids, stream: int, shape, flat: bool = False):
 
 
 def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
-           rows: Optional[np.ndarray] = None, chunk_rows: int = 1 << 17) -> np.ndarray:
+           rows: Optional[np.ndarray] = None, chunk_rows: int = 1 << 17, decide: Optional[Params] = None):
     """Radiance [len(rows), 3] (float64) of G-buffer rows (default: all).
 
     The RNG key of row p is pixel_offset + p, so a frame rendered in pieces
-    equals the frame rendered at once.
+    equals the frame rendered at once.  With opt.hard_vis and
+    opt.flip_margin > 0 returns (radiance, flip allowance), both [len(rows), 3].
     """
     P = gb["pos"].shape[0]
     rows = np.arange(P) if rows is None else np.asarray(rows)
     per = max(1, chunk_rows // (opt.n_dirs * opt.m_dirs))
-    out = []
+    pair = opt.hard_vis and opt.flip_margin > 0
+    out, allow = [], []
     with torch.no_grad():
         for s in range(0, rows.size, per):
             r = rows[s:s + per]
-            out.append(render_points(*_gbuffer_tensors(gb, r), pixel_offset + r, prm, opt).numpy())
-    return np.concatenate(out, axis=0) if out else np.zeros((0, 3))
+            res = render_points(*_gbuffer_tensors(gb, r), pixel_offset + r, prm, opt, decide=decide)
+            if pair:
+                out.append(res[0].numpy())
+                allow.append(res[1].numpy())
+            else:
+                out.append(res.numpy())
+    cat = lambda xs: np.concatenate(xs, axis=0) if xs else np.zeros((0, 3))
+    return (cat(out), cat(allow)) if pair else cat(out)
 
 
 def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
@@ -221,12 +296,14 @@ def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pi
     draw) by `rel`, and the table by 2^-11: the roundings of a bf16 MLP with
     an FP16 table, used by the BF16 tests.
     """
+    opt = dataclasses.replace(opt, flip_margin=0.0)
+    decide = prm if (opt.hard_vis and opt.decision_arith != "fp64") else None   # decisions stay those of base
     base = render(gb, prm, opt, pixel_offset, rows)
     worst = np.zeros_like(base)
     for d in range(draws):
         o = dataclasses.replace(opt, x2_jitter=rel, s_jitter=rel, mlp_jitter=rel if mlp else 0.0, jitter_seed=1 + d)
         p = _perturbed_weights(prm, rel, 1 + d) if mlp else prm
-        worst = np.maximum(worst, np.abs(render(gb, p, o, pixel_offset, rows) - base))
+        worst = np.maximum(worst, np.abs(render(gb, p, o, pixel_offset, rows, decide=decide) - base))
     return worst
 
 

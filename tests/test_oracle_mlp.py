@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 import torch
 
 import scenegen
@@ -68,3 +69,41 @@ def test_irt_outputs_and_depth_mapping():
     assert torch.allclose(t, torch.full((4,), near + (far - near) * math.log(2.0), dtype=torch.float64))
     assert float(mlp.depth_from_logit(torch.tensor(0.0, dtype=torch.float64), near, far)) == near
     assert float(mlp.depth_from_logit(torch.tensor(7.0, dtype=torch.float64), near, far)) == far
+
+
+# ---- the kernel arithmetic used for decisions (mlp3_arith) -------------------
+
+def _one_path(w1, b1, w2, b2, w3, b3):
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    return [(t([[w1]]), t([b1])), (t([[w2]]), t([b2])), (t([[w3]]), t([b3]))]
+
+
+@pytest.mark.parametrize("arith", ["bf16", "fp32"])
+def test_kernel_arith_is_exact_on_representable_values(arith):
+    # one-hot layers with power-of-two weights and bf16-representable inputs: no rounding anywhere
+    rng = np.random.default_rng(0)
+    z = torch.tensor(rng.integers(-64, 64, (16, 8)) / 32.0, dtype=torch.float64)
+    eye = lambda k, m, s: torch.tensor(np.eye(k, m) * s, dtype=torch.float64)
+    layers = [(eye(8, 8, 0.5), torch.full((8,), 0.25, dtype=torch.float64)),
+              (eye(8, 8, 2.0), torch.zeros(8, dtype=torch.float64)),
+              (eye(3, 8, -1.0), torch.tensor([0.5, 0.0, -0.25], dtype=torch.float64))]
+    np.testing.assert_array_equal(mlp.mlp3_arith(z, layers, arith).numpy(), mlp.mlp3(z, layers).numpy())
+
+
+def test_bf16_arith_rounds_inputs_hidden_weights_and_activations_only():
+    one = torch.tensor([[1.0]], dtype=torch.float64)
+    # input 1 + 2^-9 is below half an ulp of bf16 at 1 (2^-8): rounds to 1
+    z = torch.tensor([[1.0 + 2 ** -9]], dtype=torch.float64)
+    assert mlp.mlp3_arith(z, _one_path(1, 0, 1, 0, 1, 0), "bf16").item() == 1.0
+    assert mlp.mlp3(z, _one_path(1, 0, 1, 0, 1, 0)).item() == 1.0 + 2 ** -9
+    # first hidden activation 1 + 2^-7 + 2^-9 rounds to 1 + 2^-7 (nearest bf16)
+    h = mlp.mlp3_arith(one, _one_path(1 + 2 ** -7, 2 ** -9, 1, 0, 1, 0), "bf16").item()
+    assert h == 1.0 + 2 ** -7
+    # a hidden weight 1 + 2^-9 rounds to 1
+    assert mlp.mlp3_arith(one, _one_path(1, 0, 1 + 2 ** -9, 0, 1, 0), "bf16").item() == 1.0
+    # the second hidden activation and the output layer stay float32: 1 + 2^-20 survives
+    assert mlp.mlp3_arith(one, _one_path(1, 0, 1, 2 ** -20, 1, 0), "bf16").item() == 1.0 + 2 ** -20
+    assert mlp.mlp3_arith(one, _one_path(1, 0, 1, 0, 1 + 2 ** -20, 0), "bf16").item() == 1.0 + 2 ** -20
+    # fp32 rounds 1 + 2^-30 away at every stage
+    assert mlp.mlp3_arith(torch.tensor([[1.0 + 2 ** -30]], dtype=torch.float64),
+                          _one_path(1, 0, 1, 0, 1, 0), "fp32").item() == 1.0

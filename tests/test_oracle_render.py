@@ -209,3 +209,55 @@ def test_hard_visibility_with_a_constant_logit(z0, forced):
     hard = render.render(gb, _scaled_visibility_row(prm, const=z0), _opt(hard_vis=True))
     ref = render.render(gb, prm, _opt(**forced))
     np.testing.assert_allclose(hard, ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("arith, tol", [("fp32", 1e-5), ("bf16", 2e-2)])
+def test_kernel_logits_follow_the_float64_chain(arith, tol):
+    # the decision chain re-evaluated in a kernel's arithmetic stays within that
+    # arithmetic's rounding of the float64 chain (I at x, the bounce, B, I at x').
+    # Secondary logits inherit the conditioning of x' (one rounding of t can move x'
+    # across fine-level texels), so they are held to the bound on 95 % of the rows.
+    from oracle import hashgrid, mlp, sampling
+    cfg = SMALL
+    gb, prm = _setup(bias=0.2)
+    opt = _opt(hard_vis=True, decision_arith=arith)
+    rows = np.arange(cfg.n_pixels)
+    x, n, wo, alb, rough = render._gbuffer_tensors(gb, rows)
+    res = hashgrid.level_resolutions(opt.levels, opt.base_res, opt.max_res)
+    dense = hashgrid.dense_levels(res, 1 << opt.log2_T, opt.dense_coarse)
+    N, M = opt.n_dirs, opt.m_dirs
+    q = rows.astype(np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
+    z0k, z2k = render._kernel_logits(x, n, q, prm, opt, res, dense)
+    # the float64 chain, written out from the oracle's stage functions
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
+    w_i = sampling.cosine_direction(n[:, None, :], u1, u2)
+    f = hashgrid.encode(x, prm.table, res, dense)
+    f_rep = f[:, None, :].expand(-1, N, -1).reshape(-1, f.shape[1])
+    y = mlp.mlp3(torch.cat([f_rep, mlp.positional_encoding(w_i.reshape(-1, 3))], -1), prm.irt)
+    t = mlp.depth_from_logit(torch.nn.functional.softplus(y[:, 1]), opt.near, opt.far)
+    x2 = (x[:, None, :] + t.reshape(-1, N, 1) * w_i).reshape(-1, 3)
+    f2 = hashgrid.encode(x2, prm.table, res, dense)
+    _, _, n2 = mlp.brdf_decoder(f2, prm.brdf)
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q.reshape(-1, 1), 1 + np.arange(M, dtype=np.uint64)[None, :], M))
+    w_j = sampling.cosine_direction(n2[:, None, :], u1, u2)
+    f2_rep = f2[:, None, :].expand(-1, M, -1).reshape(-1, f2.shape[1])
+    z2 = mlp.mlp3(torch.cat([f2_rep, mlp.positional_encoding(w_j.reshape(-1, 3))], -1), prm.irt)[:, 0]
+    scale = float(y[:, 0].abs().max())
+    assert float((z0k.reshape(-1) - y[:, 0]).abs().max()) <= tol * scale
+    assert float(np.quantile((z2k.reshape(-1) - z2).abs().numpy(), 0.95)) <= tol * scale
+    # and the decisions agree wherever the float64 logit is clear of the rounding
+    clear = y[:, 0].abs() > tol * scale
+    assert bool(((z0k.reshape(-1) > 0) == (y[:, 0] > 0))[clear].all())
+
+
+def test_hard_flip_allowance_covers_the_float64_decisions():
+    # decisions taken in bf16 arithmetic and in float64 differ only on rows within the
+    # margin, so the float64 hard frame lies within the bf16 frame's flip allowance
+    gb, prm = _setup(bias=0.2)
+    hard64 = render.render(gb, prm, _opt(hard_vis=True))
+    hard16, allow = render.render(gb, prm, _opt(hard_vis=True, decision_arith="bf16", flip_margin=0.1))
+    assert np.all(np.abs(hard64 - hard16) <= allow + 1e-12)
+    assert np.all(allow >= 0)
+    # the bf16-decided frame keeps the scale invariance of the hit test (a power-of-two scale is exact)
+    hard16s = render.render(gb, _scaled_visibility_row(prm, scale=4.0), _opt(hard_vis=True, decision_arith="bf16"))
+    np.testing.assert_array_equal(hard16s, hard16)
