@@ -63,6 +63,7 @@ typedef enum rt_status {
 
 enum { RT_FP32 = 0, RT_BF16 = 1 };        /* precision                          */
 enum { RT_DISNEY = 0, RT_LAMBERT = 1 };   /* brdf_mode                          */
+enum { RT_VIS_SOFT = 0, RT_VIS_HARD = 1 }; /* visibility                         */
 
 /* Sizes and constants of one renderer instance.  Defaults: rt_config_default. */
 typedef struct rt_config {
@@ -81,6 +82,13 @@ typedef struct rt_config {
   float f0;              /* Schlick F0 (paper: 0.04)                            */
   float force_vis;       /* < 0: v from I; else v := force_vis  (0..1)          */
   float force_vis2;      /* < 0: v' from I; else v' := force_vis2 (0..1)        */
+  int32_t visibility;    /* RT_VIS_SOFT: Eq. 2 with v = sigmoid(z0), every
+                            direction bounces with weight 1 - v (differentiable).
+                            RT_VIS_HARD: the paper's inference (Sec. 3.2
+                            overview): v, v' = 1 when sigmoid(z0) > 0.5, else 0
+                            (a forced value counts as 1 above 0.5); only shadow
+                            directions bounce and only visible secondary
+                            directions count.  Render calls only.              */
   int32_t env_h, env_w;  /* environment map size, each 1..8192                  */
   uint64_t dir_seed;     /* SplitMix64 starting state of the direction sampler  */
 } rt_config;
@@ -193,7 +201,15 @@ rt_status rt_shade(rt_ctx* ctx, const rt_gbuffer* pts, int64_t P, int32_t level,
 
 /* Stages (a)-(e) fused in one persistent kernel: radiance [P][4] (rgb, 0) of
  * the P G-buffer points; point p uses RNG pixel id pixel_offset + p, so a
- * frame rendered in shards equals the frame rendered at once. */
+ * frame rendered in shards equals the frame rendered at once.
+ * With cfg.visibility = RT_VIS_HARD the BF16 path does the secondary work
+ * (x' encode, B, the M secondary I evaluations, Eq. 1 at x') only for shadow
+ * directions: each warpgroup queues its shadow rows in shared memory and
+ * runs them in full 128-row tiles, adding every tile's pixel sums into
+ * radiance in a fixed order (deterministic for a given launch shape; a
+ * sharded frame agrees with the whole frame up to float rounding).  It
+ * always runs 4 warpgroups per CTA.  The FP32 path takes the same decisions
+ * without compaction. */
 rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                           float* radiance, void* stream);
 
@@ -221,7 +237,8 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
                   float* radiance, void* stream, float* best_ms);
 
 /* Read or force the BF16 launch shape (lights_per_launch in {1,2,4,8},
- * warpgroups in {2,3,4}; anything else is RT_ERR_INVALID_ARG). */
+ * warpgroups in {2,3,4}; anything else is RT_ERR_INVALID_ARG).  RT_VIS_HARD
+ * renders ignore the warpgroups part (always 4). */
 rt_status rt_tuned_shape(const rt_ctx* ctx, int32_t* lights_per_launch, int32_t* warpgroups);
 rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t warpgroups);
 
@@ -229,7 +246,7 @@ rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t wa
  * (lane 3 ignored): ACCUMULATES dLoss/dtable into g_table [L][T][F] float and
  * dLoss/dweights into g_brdf / g_irt (float, blob layouts).  Sampled
  * directions are constants of the estimator.  The caller zeroes the
- * gradient buffers. */
+ * gradient buffers.  RT_VIS_HARD is not differentiable: RT_ERR_UNSUPPORTED. */
 rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                       const float* d_radiance, float* g_table, float* g_brdf, float* g_irt,
                       void* stream);

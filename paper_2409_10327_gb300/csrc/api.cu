@@ -71,6 +71,7 @@ ModelDesc model_desc(const rt_ctx* ctx) {
   m.f0 = c.f0;
   m.force_vis = c.force_vis;
   m.force_vis2 = c.force_vis2;
+  m.hard = c.visibility == RT_VIS_HARD ? 1 : 0;
   m.lambert = c.brdf_mode == RT_LAMBERT;
   m.seed = c.dir_seed;
   return m;
@@ -126,6 +127,7 @@ rt_status rt_config_default(rt_config* c) {
   c->f0 = 0.04f;
   c->force_vis = -1.0f;
   c->force_vis2 = -1.0f;
+  c->visibility = RT_VIS_SOFT;
   c->env_h = 64;
   c->env_w = 128;
   c->dir_seed = 0x5EED;
@@ -142,7 +144,8 @@ rt_status rt_config_validate(const rt_config* c) {
                   std::isfinite(c->near_t) && std::isfinite(c->far_t) && c->near_t >= 0.0f &&
                   c->far_t > c->near_t && std::isfinite(c->f0) && c->f0 >= 0.0f && c->f0 <= 1.0f &&
                   !std::isnan(c->force_vis) && c->force_vis <= 1.0f && !std::isnan(c->force_vis2) &&
-                  c->force_vis2 <= 1.0f && c->env_h >= 1 && c->env_h <= 8192 && c->env_w >= 1 &&
+                  c->force_vis2 <= 1.0f && (c->visibility == RT_VIS_SOFT || c->visibility == RT_VIS_HARD) &&
+                  c->env_h >= 1 && c->env_h <= 8192 && c->env_w >= 1 &&
                   c->env_w <= 8192;
   return ok ? RT_OK : RT_ERR_INVALID_ARG;
 }
@@ -404,7 +407,7 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
   float best = 3.0e38f;
   int best_nl = ctx->tuned_nl, best_wg = ctx->tuned_wg;
   st = RT_OK;
-  for (int wg = 2; wg <= 4 && st == RT_OK; ++wg) {
+  for (int wg = ctx->cfg.visibility == RT_VIS_HARD ? 4 : 2; wg <= 4 && st == RT_OK; ++wg) {
     for (int nl = 1; nl <= 8 && st == RT_OK; nl *= 2) {
       if (nl > 1 && nl / 2 >= E) break;   // wider launches than E lights repeat the previous shape
       float ms = 0.0f;
@@ -453,6 +456,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
   if (P < 0 || P > kMaxP || pixel_offset < 0) return RT_ERR_INVALID_ARG;
+  if (ctx->cfg.visibility == RT_VIS_HARD) return RT_ERR_UNSUPPORTED;
   if (P == 0) return RT_OK;
   if (!check_gbuffer(gb) || !check_plane(d_radiance) || g_table == nullptr || !aligned(g_table, 8) ||
       g_brdf == nullptr || !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))

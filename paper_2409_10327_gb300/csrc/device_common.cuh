@@ -197,6 +197,15 @@ __device__ __forceinline__ f3 brdf_eval(f3 albedo, float rough, f3 n, f3 wi, f3 
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 __device__ __forceinline__ float softplusf_(float z) { return z > 15.0f ? z : log1pf(expf(z)); }
+// Visibility from I's logit z0: soft sigmoid(z0) (Eq. 2 as a blend), or the
+// hit test of the paper's inference, 1 when sigmoid(z0) > 0.5, i.e. z0 > 0
+// (Sec. 3.2 overview).  A forced value (>= 0) replaces the network's; in hard
+// mode it counts as 1 above 0.5.
+__device__ __forceinline__ float visibility_from_logit(float z0, float forced, int hard) {
+  if (forced >= 0.0f) return hard ? (forced > 0.5f ? 1.0f : 0.0f) : forced;
+  return hard ? (z0 > 0.0f ? 1.0f : 0.0f) : sigmoidf_(z0);
+}
+
 __device__ __forceinline__ float depth_from_logit(float z, float near_t, float far_t) {
   return near_t + (far_t - near_t) * fminf(softplusf_(z), 1.0f);
 }

@@ -110,15 +110,23 @@ constexpr int SM_W = 0;
 constexpr int WG_FPIX = 0;                   // primary features [34][32] bf16; reused as red[128] float4
 constexpr int WG_MISC = 2560;                // mbarrier (8), then carry[NL] float4 from +16
 constexpr int WG_BYTES = 2816;
+// hard visibility: a ring of 256 queued shadow rows, the row keys of a tile and per-warp counts
+constexpr int WG_QA = 2816;                  // float4 (w_i, t) [256]
+constexpr int WG_QB = WG_QA + 256 * 16;      // int2 (pixel, i) [256]
+constexpr int WG_KEYS = WG_QB + 256 * 8;     // int [128]
+constexpr int WG_CNT = WG_KEYS + 128 * 4;    // int [4]
+constexpr int WG_BYTES_HARD = 9600;
 constexpr int SM_WG = WBF16_BYTES;
 static_assert(WG_MISC + 16 + 8 * 16 <= WG_BYTES, "warpgroup block overflow");
+static_assert(WG_CNT + 16 <= WG_BYTES_HARD, "warpgroup block overflow (hard visibility)");
 static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
 
-template <int WG>
+template <int WG, bool HARD = false>
 struct Layout {
   static constexpr int kThreads = 128 * WG;
   static constexpr int kTmemCols = WG <= 2 ? 128 * WG : 512;   // allocations are powers of two
-  static constexpr int kTmemSlot = SM_WG + WG * WG_BYTES;
+  static constexpr int kWgBytes = HARD ? WG_BYTES_HARD : WG_BYTES;
+  static constexpr int kTmemSlot = SM_WG + WG * kWgBytes;
   static constexpr size_t kSmem = kTmemSlot + 16 + 1024;
   static constexpr int kMinBlocks = WG <= 2 ? 2 : 1;
   // smallest carveout (percent of the 228 KB maximum) that holds kMinBlocks CTAs
@@ -406,22 +414,59 @@ __device__ __forceinline__ void store_pe_tmem(uint32_t x_taddr, f3 w) {
   tmem_st16(x_taddr + 16, q);
 }
 
-template <int NL, int WG>
-__global__ void __launch_bounds__(Layout<WG>::kThreads, Layout<WG>::kMinBlocks)
-render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P, long long pixel_offset,
-                   const float4* __restrict__ envs, float4* __restrict__ out) {
-  constexpr int kThreadsB = Layout<WG>::kThreads;
+// (a) f = H(x) of a tile's npix pixels into fpix [npix][32] bf16, 32
+// threads per pixel (two per level, four corners each), four pixels per pass.
+__device__ __forceinline__ void gather_primary_features(const GridDesc& g, const float4* __restrict__ pos4,
+                                                        long long p_first, int npix, int warp, int lane,
+                                                        uint8_t* fpix) {
+  for (int s0 = 0; s0 < npix; s0 += 4) {
+    const int slot = s0 + warp;
+    float2 part = make_float2(0.f, 0.f);
+    const int l = lane >> 1;
+    if (slot < npix && l < g.levels) {
+      const f3 xs = xyz(pos4[p_first + slot]);
+      const int res = g.res[l];
+      uint32_t ix, iy, iz;
+      float wx, wy, wz;
+      grid_cell(xs.x, res, ix, wx);
+      grid_cell(xs.y, res, iy, wy);
+      grid_cell(xs.z, res, iz, wz);
+      const size_t base = (size_t)l << g.log2T;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = (lane & 1) * 4 + cc;
+        const uint32_t row = corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res, g.dense[l],
+                                        g.mask);
+        const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+        const float2 v = table_entry(g, base + row);
+        part.x = fmaf(w, v.x, part.x);
+        part.y = fmaf(w, v.y, part.y);
+      }
+    }
+    part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
+    part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
+    if (slot < npix && (lane & 1) == 0)
+      *reinterpret_cast<uint32_t*>(fpix + slot * 64 + 2 * lane) = pack_bf16(part.x, part.y);
+  }
+}
+
+template <int NL, int WG, bool HARD>
+__global__ void __launch_bounds__(Layout<WG, HARD>::kThreads, Layout<WG, HARD>::kMinBlocks)
+render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ HeadParams hp, rt_gbuffer gb, int P,
+                   long long pixel_offset, const float4* __restrict__ envs, float4* __restrict__ out) {
+  using L = Layout<WG, HARD>;
+  constexpr int kThreadsB = L::kThreads;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x;
   const int wg = tid >> 7, t = tid & 127, warp = t >> 5, lane = t & 31;
   uint8_t* Wsm = sm + SM_W;
-  uint8_t* wgb = sm + SM_WG + wg * WG_BYTES;
+  uint8_t* wgb = sm + SM_WG + wg * L::kWgBytes;
   uint8_t* fpix = wgb + WG_FPIX;
   float4* red = reinterpret_cast<float4*>(wgb + WG_FPIX);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WG_MISC);
   float4* carry_s = reinterpret_cast<float4*>(wgb + WG_MISC + 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Layout<WG>::kTmemSlot);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::kTmemSlot);
 
   // ---- CTA set-up: weights into shared memory, TMEM, barriers
   for (int i = tid; i < WBF16_BYTES / 16; i += kThreadsB)
@@ -433,7 +478,7 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
   fence_async_smem();   // the weight tiles are read by the async proxy
   if (warp == 0 && wg == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(Layout<WG>::kTmemCols)
+                 "r"(L::kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -487,186 +532,370 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
     return true;
   };
 
-  for (long long sbase = p0 * N; sbase < s_end; sbase += 128) {
-    const long long p_first = sbase / N;
-    const int off0 = (int)(sbase - p_first * N);
-    const int nvalid = (int)min(128LL, s_end - sbase);
-    const int npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
-    const bool valid = t < nvalid;
-    const int local = off0 + (valid ? t : nvalid - 1);
-    const int ps = local / N;
-    const int i = local - ps * N;
-    const long long p = p_first + ps;
-
-    // (a) primary features of the tile's pixels, 32 threads per pixel (2 per level)
-    for (int g = 0; g < npix; g += 4) {
-      const int slot = g + warp;
-      float2 part = make_float2(0.f, 0.f);
-      const int l = lane >> 1;
-      if (slot < npix && l < m.grid.levels) {
-        const f3 xs = xyz(pos4[p_first + slot]);
-        const int res = m.grid.res[l];
-        uint32_t ix, iy, iz;
-        float wx, wy, wz;
-        grid_cell(xs.x, res, ix, wx);
-        grid_cell(xs.y, res, iy, wy);
-        grid_cell(xs.z, res, iz, wz);
-        const size_t base = (size_t)l << m.grid.log2T;
+  if constexpr (HARD) {
+    // Hard visibility (Sec. 3.2 overview): a primary tile adds the direct term
+    // of its visible rows and queues its shadow rows (w_i, t, pixel, i) in a
+    // ring in shared memory; every 128 queued rows make one secondary tile
+    // (x' encode, B, the M secondary I evaluations, Eq. 1 at x').  Pixel sums
+    // are added into `out` by one thread per pixel and tile, in program
+    // order, and scaled by pi/N at the end; the warpgroup owns its pixels.
+    float4* qa = reinterpret_cast<float4*>(wgb + WG_QA);
+    int2* qb = reinterpret_cast<int2*>(wgb + WG_QB);
+    int* keys = reinterpret_cast<int*>(wgb + WG_KEYS);
+    int* wcnt = reinterpret_cast<int*>(wgb + WG_CNT);
+    for (long long p = p0 + t; p < p1; p += 128)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const int c = (lane & 1) * 4 + cc;
-          const uint32_t row = corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res,
-                                          m.grid.dense[l], m.grid.mask);
-          const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
-          const float2 v = table_entry(m.grid, base + row);
-          part.x = fmaf(w, v.x, part.x);
-          part.y = fmaf(w, v.y, part.y);
+      for (int e = 0; e < NL; ++e) __stcg(out + (long long)e * P + p, make_float4(0.f, 0.f, 0.f, 0.f));
+    uint32_t qhead = 0, qtail = 0;
+    bool ok = true;
+
+    // out[e][key] += sum of c[e] over the rows with that key; rows come in key
+    // order, key < 0 marks an idle row.  One thread per key does the update.
+    auto add_rows = [&](int key, const f3 (&c)[NL]) {
+      const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool head = lane == 0 || prev != key;
+      wg_sync(wg);   // earlier readers of keys / red are done; the zeroing above is ordered
+      keys[t] = key;
+#pragma unroll
+      for (int e = 0; e < NL; ++e) {
+        f3 ce = key >= 0 ? c[e] : mk(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float ox = __shfl_down_sync(0xffffffffu, ce.x, off);
+          const float oy = __shfl_down_sync(0xffffffffu, ce.y, off);
+          const float oz = __shfl_down_sync(0xffffffffu, ce.z, off);
+          const int k2 = __shfl_down_sync(0xffffffffu, key, off);
+          if (lane + off < 32 && k2 == key) ce = mk(ce.x + ox, ce.y + oy, ce.z + oz);
+        }
+        if (e > 0) wg_sync(wg);   // the previous light's sums are read
+        red[t] = head ? make_float4(ce.x, ce.y, ce.z, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        wg_sync(wg);
+        if (key >= 0 && (t == 0 || keys[t - 1] != key)) {
+          float4 sum = red[t];
+          for (int r = ((t >> 5) + 1) << 5; r < 128 && keys[r] == key; r += 32) {
+            const float4 h = red[r];
+            sum = make_float4(sum.x + h.x, sum.y + h.y, sum.z + h.z, 0.f);
+          }
+          float4* o = out + (long long)e * P + key;
+          const float4 cur = __ldcg(o);
+          __stcg(o, make_float4(cur.x + sum.x, cur.y + sum.y, cur.z + sum.z, 0.f));
         }
       }
-      part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
-      part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
-      if (slot < npix && (lane & 1) == 0)
-        *reinterpret_cast<uint32_t*>(fpix + slot * 64 + 2 * lane) = pack_bf16(part.x, part.y);
-    }
-    wg_sync(wg);
+      wg_sync(wg);   // red (the primary-feature area) and keys are free again
+    };
 
-    const f3 x = xyz(pos4[p]);
-    const f3 n = xyz(nrm4[p]);
-    const f3 wo = xyz(view4[p]);
-    const float4 ar = ar4[p];
-    const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
-    const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
-    // Eq. 1 factors of the primary direction, fetched before the MMAs so the
-    // env-map loads overlap them
-    const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
-    const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
-    f3 le1 = mk(0.f, 0.f, 0.f);
-    if (NL == 1) le1 = env_fetch(envs, tap1);
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
-      uint32_t fr[16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint4 v = src[c];
-        fr[4 * c] = v.x;
-        fr[4 * c + 1] = v.y;
-        fr[4 * c + 2] = v.z;
-        fr[4 * c + 3] = v.w;
+    // One secondary tile over the queued rows [qhead, qhead + nvalid).
+    auto secondary = [&](int nvalid) -> bool {
+      const bool valid = t < nvalid;
+      const uint32_t slot = (qhead + (uint32_t)(valid ? t : 0)) & 255u;
+      const float4 qw = qa[slot];
+      const int2 pi = qb[slot];
+      const long long p = pi.x;
+      const f3 wi = mk(qw.x, qw.y, qw.z);
+      const f3 x = xyz(pos4[p]);
+      const f3 n = xyz(nrm4[p]);
+      const f3 wo = xyz(view4[p]);
+      const float4 ar = ar4[p];
+      const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)pi.y;
+      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      // (d) x' = x + t w_i and f' = H(x'); (b) B(f')
+      encode_point_tmem(m.grid, x + wi * qw.w, X_w);
+      if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) return false;
+      epilogue_hidden(D_w, H_w);
+      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) return false;
+      f3 n2, a2;
+      float r2;
+      {
+        float y[7];
+        head_fp32<7, 8>(D_w, &hp.bw3[0][0], hp.bb3, y);
+        const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+        n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
+        a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
+        r2 = 0.09f + 0.91f * sigmoid_fast(y[6]);
       }
-      tmem_st16(X_w, fr);
-    }
-    store_pe_tmem(X_w, wi);
+      const f3 wo2 = neg(wi);
+      const float wsec = kPi / (float)M;   // a shadow row: 1 - v = 1
+      f3 c[NL];
+#pragma unroll
+      for (int e = 0; e < NL; ++e) c[e] = mk(0.f, 0.f, 0.f);
+      // (c) + (e) at x': only visible secondary directions count
+      for (int j = 0; j < M; ++j) {
+        const f3 wj = cosine_direction_fast(n2, m.seed, dir_counter(q, M, 1 + j));
+        const EnvTap tapj = env_tap_fast(m.env_h, m.env_w, wj);
+        const f3 frw = fr1 * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+        f3 lej = mk(0.f, 0.f, 0.f);
+        if (NL == 1) lej = env_fetch(envs, tapj);
+        store_pe_tmem(X_w, wj);
+        if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) return false;
+        epilogue_hidden(D_w, H_w);
+        if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) return false;
+        const float v2 = visibility_from_logit(head_vis(D_w, hp.iw3v, hp.ib3[0]), m.force_vis2, 1);
+        const f3 wj3 = frw * (wsec * v2);
+        if (NL == 1) {
+          c[0] = c[0] + wj3 * lej;
+        } else {
+#pragma unroll
+          for (int e = 0; e < NL; ++e) c[e] = c[e] + wj3 * env_fetch(envs + e * env_hw, tapj);
+        }
+      }
+      add_rows(valid ? (int)p : -1, c);
+      return true;
+    };
 
-    // (c) I(f, w_i)
-    if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) break;
-    epilogue_hidden(D_w, H_w);
-    if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
-    float v, tdep;
-    {
-      float z[2];
-      head_fp32<2, 2>(D_w, &hp.iw3[0][0], hp.ib3, z);
-      v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
-      tdep = depth_fast(z[1], m.near_t, m.far_t);
-    }
-    // Radiance is linear in the environment map: each light's contribution of
-    // this row is fr1 (v Lenv(w_i) + (1 - v) (pi/M) sum_j v'_j fr2_j Lenv(w'_j)).
-    f3 c[NL];
-    {
-      const f3 w0 = fr1 * v;
-      if (NL == 1) {
-        c[0] = w0 * le1;
-      } else {
+    for (long long sbase = p0 * N; ok && sbase < s_end; sbase += 128) {
+      const long long p_first = sbase / N;
+      const int off0 = (int)(sbase - p_first * N);
+      const int nvalid = (int)min(128LL, s_end - sbase);
+      const int npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
+      const bool valid = t < nvalid;
+      const int local = off0 + (valid ? t : nvalid - 1);
+      const int ps = local / N;
+      const int i = local - ps * N;
+      const long long p = p_first + ps;
+
+      // (a) primary features of the tile's pixels
+      gather_primary_features(m.grid, pos4, p_first, npix, warp, lane, fpix);
+      wg_sync(wg);
+
+      const f3 x = xyz(pos4[p]);
+      const f3 n = xyz(nrm4[p]);
+      const f3 wo = xyz(view4[p]);
+      const float4 ar = ar4[p];
+      const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
+      const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
+      const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
+      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
+        uint32_t fr[16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint4 v = src[c];
+          fr[4 * c] = v.x;
+          fr[4 * c + 1] = v.y;
+          fr[4 * c + 2] = v.z;
+          fr[4 * c + 3] = v.w;
+        }
+        tmem_st16(X_w, fr);
+      }
+      store_pe_tmem(X_w, wi);
+
+      // (c) I(f, w_i): the hit test and the depth
+      if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) { ok = false; break; }
+      epilogue_hidden(D_w, H_w);
+      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) {
+        ok = false;
+        break;
+      }
+      float vis, tdep;
+      {
+        float z[2];
+        head_fp32<2, 2>(D_w, &hp.iw3[0][0], hp.ib3, z);
+        vis = visibility_from_logit(z[0], m.force_vis, 1);
+        tdep = depth_fast(z[1], m.near_t, m.far_t);
+      }
+      // visible rows: the direct term of Eq. 2
+      {
+        f3 c[NL];
+        const f3 w0 = fr1 * vis;
 #pragma unroll
         for (int e = 0; e < NL; ++e) c[e] = w0 * env_fetch(envs + e * env_hw, tap1);
+        add_rows(valid ? (int)p : -1, c);
       }
-    }
-
-    // (d) bounce: x' = x + t w_i; f' = H(x') into X columns 0..15
-    encode_point_tmem(m.grid, x + wi * tdep, X_w);
-
-    // (b) B(f')
-    if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) break;
-    epilogue_hidden(D_w, H_w);
-    if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) break;
-    f3 n2, a2;
-    float r2;
-    {
-      float y[7];
-      head_fp32<7, 8>(D_w, &hp.bw3[0][0], hp.bb3, y);
-      const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
-      n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
-      a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
-      r2 = 0.09f + 0.91f * sigmoid_fast(y[6]);
-    }
-    const f3 wo2 = neg(wi);
-    const float wsec = (1.0f - v) * (kPi / (float)M);
-
-    // (c) + (e) at x': M directions about n'
-    bool ok = true;
-    for (int j = 0; j < M && ok; ++j) {
-      const f3 wj = cosine_direction_fast(n2, m.seed, dir_counter(q, M, 1 + j));
-      const EnvTap tapj = env_tap_fast(m.env_h, m.env_w, wj);
-      const f3 frw = fr1 * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
-      f3 lej = mk(0.f, 0.f, 0.f);
-      if (NL == 1) lej = env_fetch(envs, tapj);
-      store_pe_tmem(X_w, wj);
-      ok = run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); });
-      if (!ok) break;
-      epilogue_hidden(D_w, H_w);
-      ok = run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
-      if (!ok) break;
-      const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(head_vis(D_w, hp.iw3v, hp.ib3[0]));
-      const f3 wj3 = frw * (wsec * v2);
-      if (NL == 1) {
-        c[0] = c[0] + wj3 * lej;
-      } else {
-#pragma unroll
-        for (int e = 0; e < NL; ++e) c[e] = c[e] + wj3 * env_fetch(envs + e * env_hw, tapj);
-      }
-    }
-    if (!ok) break;
-
-    // deterministic segmented reduction of the tile's rows into their pixels,
-    // one light at a time
-    const int key = valid ? ps : -1;
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = lane == 0 || prev != key;
-#pragma unroll
-    for (int e = 0; e < NL; ++e) {
-      f3 ce = valid ? c[e] : mk(0.f, 0.f, 0.f);
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float ox = __shfl_down_sync(0xffffffffu, ce.x, off);
-        const float oy = __shfl_down_sync(0xffffffffu, ce.y, off);
-        const float oz = __shfl_down_sync(0xffffffffu, ce.z, off);
-        const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
-        if (lane + off < 32 && ok2 == key) ce = mk(ce.x + ox, ce.y + oy, ce.z + oz);
-      }
-      wg_sync(wg);   // fpix reads (first light) or the previous light's sums are done
-      red[t] = head ? make_float4(ce.x, ce.y, ce.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+      // shadow rows join the queue in row order
+      const bool shadow = valid && vis == 0.0f;
+      const unsigned bal = __ballot_sync(0xffffffffu, shadow);
+      if (lane == 0) wcnt[warp] = __popc(bal);
       wg_sync(wg);
-      if (t < npix) {
-        const int ra = max(0, t * N - off0);
-        const int rb = min(nvalid, (t + 1) * N - off0);
-        f3 sum = mk(0.f, 0.f, 0.f);
-        if (t == 0) {
-          const float4 cs = carry_s[e];
-          sum = mk(cs.x, cs.y, cs.z);
-        }
-        for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
-          const float4 h = red[r];
-          sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
-        }
-        const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
-        if (complete) {
-          const float sc = kPi / (float)N;
-          out[(long long)e * P + p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
-        }
-        if (t == npix - 1)
-          carry_s[e] = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
+      int before = 0, total = 0;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int cw = wcnt[w];
+        before += w < warp ? cw : 0;
+        total += cw;
       }
+      if (shadow) {
+        const uint32_t slot = (qtail + (uint32_t)(before + __popc(bal & ((1u << lane) - 1u)))) & 255u;
+        qa[slot] = make_float4(wi.x, wi.y, wi.z, tdep);
+        qb[slot] = make_int2((int)p, i);
+      }
+      qtail += (uint32_t)total;
+      wg_sync(wg);   // the new entries are visible; wcnt is free
+      while (ok && qtail - qhead >= 128u) {
+        ok = secondary(128);
+        qhead += 128u;
+      }
+    }
+    if (ok && qtail != qhead) {
+      ok = secondary((int)(qtail - qhead));
+      qhead = qtail;
     }
     wg_sync(wg);
+    if (ok) {
+      const float sc = kPi / (float)N;
+      for (long long p = p0 + t; p < p1; p += 128)
+#pragma unroll
+        for (int e = 0; e < NL; ++e) {
+          float4* o = out + (long long)e * P + p;
+          const float4 v = __ldcg(o);
+          __stcg(o, make_float4(v.x * sc, v.y * sc, v.z * sc, 0.f));
+        }
+    }
+  } else {
+    for (long long sbase = p0 * N; sbase < s_end; sbase += 128) {
+      const long long p_first = sbase / N;
+      const int off0 = (int)(sbase - p_first * N);
+      const int nvalid = (int)min(128LL, s_end - sbase);
+      const int npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
+      const bool valid = t < nvalid;
+      const int local = off0 + (valid ? t : nvalid - 1);
+      const int ps = local / N;
+      const int i = local - ps * N;
+      const long long p = p_first + ps;
+
+      // (a) primary features of the tile's pixels
+      gather_primary_features(m.grid, pos4, p_first, npix, warp, lane, fpix);
+      wg_sync(wg);
+
+      const f3 x = xyz(pos4[p]);
+      const f3 n = xyz(nrm4[p]);
+      const f3 wo = xyz(view4[p]);
+      const float4 ar = ar4[p];
+      const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
+      const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
+      // Eq. 1 factors of the primary direction, fetched before the MMAs so the
+      // env-map loads overlap them
+      const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
+      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      f3 le1 = mk(0.f, 0.f, 0.f);
+      if (NL == 1) le1 = env_fetch(envs, tap1);
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
+        uint32_t fr[16];
+  #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint4 v = src[c];
+          fr[4 * c] = v.x;
+          fr[4 * c + 1] = v.y;
+          fr[4 * c + 2] = v.z;
+          fr[4 * c + 3] = v.w;
+        }
+        tmem_st16(X_w, fr);
+      }
+      store_pe_tmem(X_w, wi);
+
+      // (c) I(f, w_i)
+      if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) break;
+      epilogue_hidden(D_w, H_w);
+      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
+      float v, tdep;
+      {
+        float z[2];
+        head_fp32<2, 2>(D_w, &hp.iw3[0][0], hp.ib3, z);
+        v = m.force_vis >= 0.f ? m.force_vis : sigmoid_fast(z[0]);
+        tdep = depth_fast(z[1], m.near_t, m.far_t);
+      }
+      // Radiance is linear in the environment map: each light's contribution of
+      // this row is fr1 (v Lenv(w_i) + (1 - v) (pi/M) sum_j v'_j fr2_j Lenv(w'_j)).
+      f3 c[NL];
+      {
+        const f3 w0 = fr1 * v;
+        if (NL == 1) {
+          c[0] = w0 * le1;
+        } else {
+  #pragma unroll
+          for (int e = 0; e < NL; ++e) c[e] = w0 * env_fetch(envs + e * env_hw, tap1);
+        }
+      }
+
+      // (d) bounce: x' = x + t w_i; f' = H(x') into X columns 0..15
+      encode_point_tmem(m.grid, x + wi * tdep, X_w);
+
+      // (b) B(f')
+      if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) break;
+      epilogue_hidden(D_w, H_w);
+      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) break;
+      f3 n2, a2;
+      float r2;
+      {
+        float y[7];
+        head_fp32<7, 8>(D_w, &hp.bw3[0][0], hp.bb3, y);
+        const float ninv = rsqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+        n2 = mk(y[0] * ninv, y[1] * ninv, y[2] * ninv);
+        a2 = mk(sigmoid_fast(y[3]), sigmoid_fast(y[4]), sigmoid_fast(y[5]));
+        r2 = 0.09f + 0.91f * sigmoid_fast(y[6]);
+      }
+      const f3 wo2 = neg(wi);
+      const float wsec = (1.0f - v) * (kPi / (float)M);
+
+      // (c) + (e) at x': M directions about n'
+      bool ok = true;
+      for (int j = 0; j < M && ok; ++j) {
+        const f3 wj = cosine_direction_fast(n2, m.seed, dir_counter(q, M, 1 + j));
+        const EnvTap tapj = env_tap_fast(m.env_h, m.env_w, wj);
+        const f3 frw = fr1 * brdf_eval_fast(a2, r2, n2, wj, wo2, m.f0, m.lambert);
+        f3 lej = mk(0.f, 0.f, 0.f);
+        if (NL == 1) lej = env_fetch(envs, tapj);
+        store_pe_tmem(X_w, wj);
+        ok = run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); });
+        if (!ok) break;
+        epilogue_hidden(D_w, H_w);
+        ok = run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); });
+        if (!ok) break;
+        const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoid_fast(head_vis(D_w, hp.iw3v, hp.ib3[0]));
+        const f3 wj3 = frw * (wsec * v2);
+        if (NL == 1) {
+          c[0] = c[0] + wj3 * lej;
+        } else {
+  #pragma unroll
+          for (int e = 0; e < NL; ++e) c[e] = c[e] + wj3 * env_fetch(envs + e * env_hw, tapj);
+        }
+      }
+      if (!ok) break;
+
+      // deterministic segmented reduction of the tile's rows into their pixels,
+      // one light at a time
+      const int key = valid ? ps : -1;
+      const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool head = lane == 0 || prev != key;
+  #pragma unroll
+      for (int e = 0; e < NL; ++e) {
+        f3 ce = valid ? c[e] : mk(0.f, 0.f, 0.f);
+  #pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float ox = __shfl_down_sync(0xffffffffu, ce.x, off);
+          const float oy = __shfl_down_sync(0xffffffffu, ce.y, off);
+          const float oz = __shfl_down_sync(0xffffffffu, ce.z, off);
+          const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
+          if (lane + off < 32 && ok2 == key) ce = mk(ce.x + ox, ce.y + oy, ce.z + oz);
+        }
+        wg_sync(wg);   // fpix reads (first light) or the previous light's sums are done
+        red[t] = head ? make_float4(ce.x, ce.y, ce.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        wg_sync(wg);
+        if (t < npix) {
+          const int ra = max(0, t * N - off0);
+          const int rb = min(nvalid, (t + 1) * N - off0);
+          f3 sum = mk(0.f, 0.f, 0.f);
+          if (t == 0) {
+            const float4 cs = carry_s[e];
+            sum = mk(cs.x, cs.y, cs.z);
+          }
+          for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
+            const float4 h = red[r];
+            sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
+          }
+          const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
+          if (complete) {
+            const float sc = kPi / (float)N;
+            out[(long long)e * P + p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
+          }
+          if (t == npix - 1)
+            carry_s[e] = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
+        }
+      }
+      wg_sync(wg);
+    }
+
   }
 
   // ---- teardown: drain, then free TMEM
@@ -676,61 +905,65 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   if (warp == 0 && wg == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(Layout<WG>::kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tslot), "r"(L::kTmemCols)
                  : "memory");
 }
 
-template <int NL, int WG>
+template <int NL, int WG, bool HARD>
 cudaError_t prepare_variant() {
-  cudaError_t e = cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Layout<WG>::kSmem);
+  using L = Layout<WG, HARD>;
+  cudaError_t e = cudaFuncSetAttribute(render_bf16_kernel<NL, WG, HARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::kSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(render_bf16_kernel<NL, WG>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              Layout<WG>::kCarveout);
+  return cudaFuncSetAttribute(render_bf16_kernel<NL, WG, HARD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              L::kCarveout);
 }
 
-template <int NL, int WG>
+template <int NL, int WG, bool HARD>
 cudaError_t launch_variant(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P, long long offset,
                            const float4* envs, float4* out, int num_sms, cudaStream_t s) {
-  const long long per_sm = Layout<WG>::kMinBlocks;
+  using L = Layout<WG, HARD>;
+  const long long per_sm = L::kMinBlocks;
   const long long want = ((long long)P + WG - 1) / WG;
   const int grid = (int)(want < per_sm * num_sms ? want : per_sm * num_sms);
-  render_bf16_kernel<NL, WG><<<grid, Layout<WG>::kThreads, Layout<WG>::kSmem, s>>>(m, hp, gb, P, offset, envs, out);
+  render_bf16_kernel<NL, WG, HARD><<<grid, L::kThreads, L::kSmem, s>>>(m, hp, gb, P, offset, envs, out);
   return cudaGetLastError();
 }
 
-template <int WG>
+template <int WG, bool HARD>
 cudaError_t launch_lights(int nl, const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                           long long offset, const float4* envs, float4* out, int num_sms, cudaStream_t s) {
   switch (nl) {
-    case 8: return launch_variant<8, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
-    case 4: return launch_variant<4, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
-    case 2: return launch_variant<2, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
-    default: return launch_variant<1, WG>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    case 8: return launch_variant<8, WG, HARD>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    case 4: return launch_variant<4, WG, HARD>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    case 2: return launch_variant<2, WG, HARD>(m, hp, gb, P, offset, envs, out, num_sms, s);
+    default: return launch_variant<1, WG, HARD>(m, hp, gb, P, offset, envs, out, num_sms, s);
   }
+}
+
+template <int WG, bool HARD>
+cudaError_t prepare_wg() {
+  cudaError_t e = prepare_variant<1, WG, HARD>();
+  e = e != cudaSuccess ? e : prepare_variant<2, WG, HARD>();
+  e = e != cudaSuccess ? e : prepare_variant<4, WG, HARD>();
+  e = e != cudaSuccess ? e : prepare_variant<8, WG, HARD>();
+  return e;
 }
 
 }  // namespace
 
-template <int WG>
-cudaError_t prepare_wg() {
-  cudaError_t e = prepare_variant<1, WG>();
-  e = e != cudaSuccess ? e : prepare_variant<2, WG>();
-  e = e != cudaSuccess ? e : prepare_variant<4, WG>();
-  e = e != cudaSuccess ? e : prepare_variant<8, WG>();
-  return e;
-}
-
 cudaError_t prepare_render_bf16() {
-  cudaError_t e = prepare_wg<2>();
-  e = e != cudaSuccess ? e : prepare_wg<3>();
-  e = e != cudaSuccess ? e : prepare_wg<4>();
+  cudaError_t e = prepare_wg<2, false>();
+  e = e != cudaSuccess ? e : prepare_wg<3, false>();
+  e = e != cudaSuccess ? e : prepare_wg<4, false>();
+  e = e != cudaSuccess ? e : prepare_wg<4, true>();
   return e;
 }
 
 // E lights in launches of up to `max_nl` (1, 2, 4 or 8) lights each; light e
 // reads envs + e * env_h * env_w and writes out + e * P.  Every launch
-// recomputes the geometry, so fewer, wider launches share more work.
+// recomputes the geometry, so fewer, wider launches share more work.  Hard
+// visibility always runs 4 warpgroups per CTA.
 cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                       long long offset, const float4* envs, int E, float4* out, int num_sms,
                                       int max_nl, int wg, cudaStream_t s) {
@@ -742,9 +975,10 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
     mm.env = envs + e0 * hw;
     const float4* ee = envs + e0 * hw;
     float4* oo = out + (long long)e0 * P;
-    const cudaError_t err = wg == 2   ? launch_lights<2>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
-                            : wg == 4 ? launch_lights<4>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
-                                      : launch_lights<3>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s);
+    const cudaError_t err = m.hard    ? launch_lights<4, true>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
+                            : wg == 2 ? launch_lights<2, false>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
+                            : wg == 3 ? launch_lights<3, false>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s)
+                                      : launch_lights<4, false>(nl, mm, hp, gb, P, offset, ee, oo, num_sms, s);
     if (err != cudaSuccess) return err;
     e0 += nl;
   }
@@ -753,7 +987,8 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 
 cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                long long offset, float4* out, int num_sms, cudaStream_t s) {
-  return launch_variant<1, 4>(m, hp, gb, P, offset, m.env, out, num_sms, s);
+  return m.hard ? launch_variant<1, 4, true>(m, hp, gb, P, offset, m.env, out, num_sms, s)
+                : launch_variant<1, 4, false>(m, hp, gb, P, offset, m.env, out, num_sms, s);
 }
 
 }  // namespace rtk

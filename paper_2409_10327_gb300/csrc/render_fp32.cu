@@ -108,7 +108,7 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
       store_relu_colbias(actA, acc, sw + OFF_IB2, rg, cg);
       __syncwarp();
       const float2 z = irt_head(actA, sw, lane);
-      const float v = m.force_vis >= 0.f ? m.force_vis : sigmoidf_(z.x);
+      const float v = visibility_from_logit(z.x, m.force_vis, m.hard);
       const float t = depth_from_logit(z.y, m.near_t, m.far_t);
 
       // (d) bounce: x' = x + t w_i, f' = H(x')
@@ -176,7 +176,7 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
         store_relu_colbias(actA, acc, sw + OFF_IB2, rg, cg);
         __syncwarp();
         const float z0 = irt_head(actA, sw, lane).x;
-        const float v2 = m.force_vis2 >= 0.f ? m.force_vis2 : sigmoidf_(z0);
+        const float v2 = visibility_from_logit(z0, m.force_vis2, m.hard);
         const f3 le = env_lookup(m.env, m.env_h, m.env_w, wj);
         const f3 fr = brdf_eval(a2, r2, n2, wj, wo2, m.f0, m.lambert);
         lo2 = lo2 + (le * fr) * v2;

@@ -85,6 +85,7 @@ struct ModelDesc {
   int N, M;
   float near_t, far_t, f0;
   float force_vis, force_vis2;
+  int hard;                    // 1: hard visibility (RT_VIS_HARD)
   int lambert;
   uint64_t seed;
 };

@@ -107,6 +107,7 @@ extern "C" rt_status rt_render_frame_static(const rt_config* cfg, const void* ta
   m.f0 = cfg->f0;
   m.force_vis = cfg->force_vis;
   m.force_vis2 = cfg->force_vis2;
+  m.hard = cfg->visibility == RT_VIS_HARD ? 1 : 0;
   m.lambert = cfg->brdf_mode == RT_LAMBERT;
   m.seed = cfg->dir_seed;
 
