@@ -301,6 +301,26 @@ def run_ours(args, cfg):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     h2d = sum(v.numel() * v.element_size() for v in host_gb[0].values())
     d2h = host_out.numel() * host_out.element_size()
+
+    # the spatial SVGF denoiser (Sec. 4.1) on the rendered frame; depth = distance to a camera at (0, 0, -3)
+    den = None
+    if not args.no_denoise and cfg.width * cfg.height == cfg.n_pixels:
+        from paper_2409_10327_gb300 import binding
+        depth = (gbs[0]["pos"][:, :3] - torch.tensor([0.0, 0.0, -3.0], device="cuda")).norm(dim=1).contiguous()
+        d_out = torch.empty_like(out)
+        d_work = torch.empty_like(out)
+        for _ in range(3):
+            binding.denoise(out, depth, gbs[0]["normal"], cfg.width, cfg.height, out=d_out, work=d_work)
+        reps = 20
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(reps):
+            binding.denoise(out, depth, gbs[0]["normal"], cfg.width, cfg.height, out=d_out, work=d_work)
+        d1.record(stream)
+        barrier()
+        den = {"ms": d0.elapsed_time(d1) / reps, "iterations": 5, "launches": 6,
+               "image": f"{cfg.width}x{cfg.height}", "note": "spatial SVGF, L2-resident image, CUDA events over 20 runs"}
     for r in renderers:
         r.close()
     del renderers, gbs, host_gb, staging
@@ -362,7 +382,7 @@ def run_ours(args, cfg):
             "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard,
+            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "denoise": den,
             "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
                           "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
@@ -443,6 +463,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hard", action="store_true", help="skip the hard-visibility timing")
+    ap.add_argument("--no-denoise", action="store_true", help="skip the denoiser timing")
     ap.add_argument("--mode", choices=["frame", "serve"], default="frame")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)

@@ -279,6 +279,35 @@ rt_status rt_render_frame_static(const rt_config* cfg, const void* table, const 
                                  const float* env, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                                  float* radiance, void* stream);
 
+/* ---- denoising --------------------------------------------------------- */
+
+/* Spatial SVGF (Schied et al. 2017) with its temporal parts removed, as the
+ * paper applies it to the raw Monte Carlo frame (Sec. 4.1).  Needs no
+ * context.  For the width x height image (pixel p = y * width + x):
+ *   radiance [P][4] float (rgb used), depth [P] float, normal [P][4] float
+ *   (unit xyz used), all device, float4 planes 16-byte aligned;
+ *   work [P][4] float scratch, out [P][4] float: denoised rgb and the
+ *   filtered luminance variance in lane 3.  radiance, work and out must not
+ *   overlap.
+ * First the luminance variance from 7 x 7 moments weighted by
+ *   w_z = exp(-|z(p) - z(q)| / (sigma_z |grad z(p) . (q - p)| + 1e-10)) and
+ *   w_n = max(0, n(p) . n(q))^sigma_n, grad z by one-pixel forward
+ *   differences of the depth map (backward at the last column / row; the
+ *   paper's "offset" depth gradient, supplementary "Rendering Details");
+ * then `iterations` a-trous passes (step 2^i, 5 x 5 taps of the B3 spline
+ *   [1, 4, 6, 4, 1] / 16 in each axis) with weights h w_z w_n w_l,
+ *   w_l = exp(-|l(p) - l(q)| / (sigma_l sqrt(g(p)) + 1e-10)), l the
+ *   luminance (0.2126, 0.7152, 0.0722) and g the 3 x 3 Gaussian of the
+ *   variance: c' = sum w c / sum w, Var' = sum w^2 Var / (sum w)^2.  Taps
+ *   outside the image are skipped.  SVGF's defaults: iterations 5,
+ *   sigma_z 1, sigma_n 128, sigma_l 4.
+ * width, height >= 1 with width * height < 2^31; iterations 0..12; sigmas
+ * finite, sigma_z, sigma_l > 0, sigma_n >= 0; else RT_ERR_INVALID_ARG.
+ * 1 + iterations launches on `stream`; no allocation. */
+rt_status rt_denoise(int32_t width, int32_t height, const float* radiance, const float* depth, const float* normal,
+                     int32_t iterations, float sigma_z, float sigma_n, float sigma_l, float* work, float* out,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

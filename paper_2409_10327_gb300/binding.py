@@ -28,7 +28,7 @@ EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level
            "rt_level_is_dense", "rt_param_count", "rt_workspace_bytes", "rt_create", "rt_destroy",
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
            "rt_render_frame", "rt_backward", "rt_render_frame_static", "rt_render_frame_multi", "rt_tune",
-           "rt_tuned_shape", "rt_set_launch_shape"]
+           "rt_tuned_shape", "rt_set_launch_shape", "rt_denoise"]
 
 
 class RtConfig(ctypes.Structure):
@@ -56,7 +56,7 @@ def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2409_10327_gb300.build`")
     lib = ctypes.CDLL(LIB_PATH)
-    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    P, I32, I64, U32, F32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
     cfgp = ctypes.POINTER(RtConfig)
     sig = {
         "rt_status_str": (ctypes.c_char_p, [I32]),
@@ -82,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "rt_tune": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, I32, P, P, ctypes.POINTER(ctypes.c_float)]),
         "rt_tuned_shape": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "rt_set_launch_shape": (I32, [P, I32, I32]),
+        "rt_denoise": (I32, [I32, I32, P, P, P, I32, F32, F32, F32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -147,6 +148,18 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def _stream() -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def denoise(radiance: torch.Tensor, depth: torch.Tensor, normal: torch.Tensor, width: int, height: int,
+            iterations: int = 5, sigma_z: float = 1.0, sigma_n: float = 128.0, sigma_l: float = 4.0,
+            out: Optional[torch.Tensor] = None, work: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """rt_denoise: spatial SVGF of a width x height frame; returns [P, 4] (rgb, variance)."""
+    P = width * height
+    out = torch.empty(P, 4, device=radiance.device, dtype=torch.float32) if out is None else out
+    work = torch.empty(P, 4, device=radiance.device, dtype=torch.float32) if work is None else work
+    _check("rt_denoise", LIB.rt_denoise(width, height, _ptr(radiance), _ptr(depth), _ptr(normal), iterations,
+                                        sigma_z, sigma_n, sigma_l, _ptr(work), _ptr(out), _stream()))
+    return out
 
 
 def gbuffer(gb: Dict[str, torch.Tensor]) -> RtGbuffer:

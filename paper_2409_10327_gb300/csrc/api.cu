@@ -467,3 +467,27 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
 }
 
 }  // extern "C"
+
+rt_status rt_denoise(int32_t width, int32_t height, const float* radiance, const float* depth, const float* normal,
+                     int32_t iterations, float sigma_z, float sigma_n, float sigma_l, float* work, float* out,
+                     void* stream) {
+  if (width < 1 || height < 1 || (int64_t)width * height > kMaxP || iterations < 0 || iterations > 12)
+    return RT_ERR_INVALID_ARG;
+  if (!std::isfinite(sigma_z) || !std::isfinite(sigma_n) || !std::isfinite(sigma_l) || !(sigma_z > 0.0f) ||
+      !(sigma_l > 0.0f) || !(sigma_n >= 0.0f))
+    return RT_ERR_INVALID_ARG;
+  if (!check_plane(radiance) || depth == nullptr || !aligned(depth, 4) || !check_plane(normal) ||
+      !check_plane(work) || !check_plane(out))
+    return RT_ERR_INVALID_ARG;
+  const int64_t bytes = (int64_t)width * height * 16;
+  auto overlap = [&](const float* a, const float* b) {
+    const char* x = reinterpret_cast<const char*>(a);
+    const char* y = reinterpret_cast<const char*>(b);
+    return x < y + bytes && y < x + bytes;
+  };
+  if (overlap(radiance, work) || overlap(radiance, out) || overlap(work, out)) return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_denoise(width, height, reinterpret_cast<const float4*>(radiance), depth,
+                                    reinterpret_cast<const float4*>(normal), iterations, sigma_z, sigma_n, sigma_l,
+                                    reinterpret_cast<float4*>(work), reinterpret_cast<float4*>(out),
+                                    (cudaStream_t)stream));
+}

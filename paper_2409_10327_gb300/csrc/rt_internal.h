@@ -127,6 +127,8 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                float4* out, int num_sms, cudaStream_t s);
+cudaError_t launch_denoise(int W, int H, const float4* rad, const float* z, const float4* nrm, int iterations,
+                           float sigma_z, float sigma_n, float sigma_l, float4* work, float4* out, cudaStream_t s);
 cudaError_t launch_backward_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                  const float4* dL, float* g_table, float* g_brdf, float* g_irt, int num_sms,
                                  cudaStream_t s);
