@@ -253,6 +253,74 @@ def _roofline(cfg, launch_ms, peaks):
     return roof
 
 
+def backward_flop_per_sample(cfg) -> int:
+    """Algorithmic FLOPs of one secondary sample's adjoint: the forward recomputed plus, per
+    layer, the input gradient and the weight gradient (each as many MACs as the forward)."""
+    return 3 * algorithmic_flop_per_sample(cfg)
+
+
+def time_backward(steps: int, warmup: int, barrier, rays: int = 0):
+    """One distillation step on the 65,536-ray x 64-direction batch (FP32): the student's forward,
+    dLoss/dL = (L_s - L_t) / (3 P) against a random-weight teacher of the same architecture
+    (teacher seed 1, student seed 2), and rt_backward into zeroed gradient buffers."""
+    import torch
+    from paper_2409_10327_gb300 import binding
+    cfg = scenegen.CONFIGS["grad65k"]
+    if rays:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, width=rays, height=1)
+    gb = {k: torch.from_numpy(v).cuda() for k, v in scenegen.make_gbuffer(cfg.n_pixels, 3).items()}
+
+    def renderer(seed):
+        sc = scenegen.make_scene(cfg, seed, bias_scale=0.1)
+        r = binding.Renderer(binding.make_config(cfg))
+        r.set_params(torch.from_numpy(sc.table).cuda(), torch.from_numpy(sc.brdf_blob).cuda(),
+                     torch.from_numpy(sc.irt_blob).cuda(), torch.from_numpy(sc.env).cuda())
+        return r, sc
+    teacher, _ = renderer(1)
+    student, sc = renderer(2)
+    target = teacher.render_frame(gb)
+    g_t = torch.zeros(sc.table.size, device="cuda")
+    g_b = torch.zeros(sc.brdf_blob.size, device="cuda")
+    g_i = torch.zeros(sc.irt_blob.size, device="cuda")
+    out = torch.empty_like(target)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        student.render_frame(gb, out=out)
+        d = (out - target) / (3.0 * cfg.n_pixels)
+        d[:, 3] = 0.0
+        g_t.zero_(), g_b.zero_(), g_i.zero_()
+        if ev is not None:
+            ev[0].record(stream)
+        student.backward(gb, d, g_t, g_b, g_i)
+        if ev is not None:
+            ev[1].record(stream)
+    for _ in range(warmup):
+        step()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0.record(stream)
+    for k in range(steps):
+        step(evs[k])
+    t1.record(stream)
+    barrier()
+    total = t0.elapsed_time(t1)
+    bwd = [a.elapsed_time(b) for a, b in evs]
+    avg_s = sum(bwd) / len(bwd) / 1e3
+    flop = backward_flop_per_sample(cfg) * cfg.samples
+    teacher.close()
+    student.close()
+    return {"workload": f"grad65k: {cfg.n_pixels:,} rays x 64 directions, M=8, L=16, T=2^19, fp32, L2 distillation",
+            "ms_per_step": total / steps, "backward_ms": statistics.median(bwd),
+            "value": cfg.samples * steps / (total / 1e3), "unit": UNIT, "steps": steps,
+            "roofline": {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flop / avg_s / 1e12 / FP32_ALU_PEAK_TFLOPS,
+                         "algorithmic_per_launch": flop, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}}
+
+
 def run_ours(args, cfg):
     import dataclasses
     import torch
@@ -361,6 +429,9 @@ def run_ours(args, cfg):
         for r in rs:
             r.close()
 
+    # row a10: one distillation step (forward + hand-written adjoint)
+    bwd = None if args.no_backward else time_backward(max(3, args.steps // 4), args.warmup, barrier)
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -382,7 +453,7 @@ def run_ours(args, cfg):
             "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "denoise": den,
+            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "denoise": den, "backward": bwd,
             "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
                           "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
@@ -464,7 +535,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hard", action="store_true", help="skip the hard-visibility timing")
     ap.add_argument("--no-denoise", action="store_true", help="skip the denoiser timing")
-    ap.add_argument("--mode", choices=["frame", "serve"], default="frame")
+    ap.add_argument("--no-backward", action="store_true", help="skip the backward (distillation step) timing")
+    ap.add_argument("--mode", choices=["frame", "serve", "backward"], default="frame")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)
     ap.add_argument("--pixels", type=int, default=0,
@@ -478,6 +550,12 @@ def main():
         run_reference(args, cfg)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "backward":
+        import torch
+        torch.cuda.set_device(0)
+        line = time_backward(args.steps, args.warmup, torch.cuda.synchronize, rays=args.pixels)
+        print(json.dumps({"metric": "backward (distillation step) secondary samples/s", "n_gpus": 1,
+                          "warmup": args.warmup, "dtype": "f32", "data": "synthetic", **line}))
     else:
         run_ours(args, cfg)
 
