@@ -45,12 +45,13 @@ the detached n'_i.  Pins: central finite differences of this forward
 from __future__ import annotations
 
 import dataclasses
+import math
 from typing import Dict, Optional
 
 import numpy as np
 import torch
 
-from . import hashgrid, mlp, sampling, shading
+from . import hashgrid, mis, mlp, sampling, shading
 
 
 @dataclasses.dataclass(frozen=True)
@@ -68,6 +69,7 @@ class Options:
     force_vis: float = -1.0      # < 0: use I's visibility
     force_vis2: float = -1.0
     hard_vis: bool = False       # v, v' = 1[sigma(z0) > 0.5] (Sec. 3.2 overview)
+    sampling: str = "cosine"     # primary directions: 'cosine' or 'mis' (light + GGX, balance heuristic; mis.py)
     decision_arith: str = "fp64"  # arithmetic of the hard decisions: 'fp64', 'fp32' or 'bf16'
     flip_margin: float = 0.0     # > 0: also return the flip allowance of rows with |z0| < margin
     dir_seed: int = 0x5EED
@@ -114,7 +116,34 @@ def _gbuffer_tensors(gb: Dict[str, np.ndarray], rows: np.ndarray):
     return g("pos", 3), g("normal", 3), g("view", 3), ar[:, :3], ar[:, 3]
 
 
-def _kernel_logits(x, n, q, prm: Params, opt: Options, res, dense):
+def _primary_dirs(x, n, wo, rough, q, prm: Params, opt: Options, jitter=None):
+    """Primary directions w_i [P, N, 3] and their Eq. 1 weights relative to cosine sampling.
+
+    Cosine sampling: the weight is None ((w . n) / p = pi).  MIS: the factor
+    (n . w)+ / (n_L p_L + n_G p_G) times N / pi, so that (pi / N) sum stays the
+    estimator's form.  `jitter` [P, N, 3] (conditioning probe only) is added to
+    the sphere point of a cosine sample or to an MIS direction.
+    """
+    N, M = opt.n_dirs, opt.m_dirs
+    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
+    if opt.sampling == "cosine":
+        return sampling.cosine_direction(n[:, None, :], u1, u2, jitter), None
+    marg, cond = mis.env_cdf(prm.env.detach().numpy()[..., :3].astype(np.float32))
+    w, fac = mis.primary_directions(n, wo, rough, u1, u2, N, marg, cond)
+    if jitter is not None:
+        w = w + jitter
+        w = w / w.norm(dim=-1, keepdim=True)
+        nv = n[:, None, :].expand_as(w)
+        wv = wo[:, None, :].expand_as(w)
+        alpha = (rough * rough)[:, None].expand(w.shape[:2])
+        n_g = torch.where((n * wo).sum(-1) > mis.NOV_MIN, torch.full_like(rough, N // 2),
+                          torch.zeros_like(rough))[:, None]
+        den = (N - n_g) * mis.pdf_light(w, marg, cond) + n_g * mis.pdf_ggx(w, nv, wv, alpha)
+        fac = torch.clamp((nv * w).sum(-1), min=0.0) / den
+    return w, fac * (N / math.pi)
+
+
+def _kernel_logits(x, n, wo, rough, q, prm: Params, opt: Options, res, dense):
     """Visibility logits z0 [P, N] and z0' [P*N, M] as a kernel computes them.
 
     The chain that leads to the decisions (f, I, the bounce, f', B, the
@@ -125,8 +154,7 @@ def _kernel_logits(x, n, q, prm: Params, opt: Options, res, dense):
     """
     arith = opt.decision_arith
     P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
-    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
-    w_i = sampling.cosine_direction(n[:, None, :], u1, u2)                    # unjittered, [P, N, 3]
+    w_i, _ = _primary_dirs(x, n, wo, rough, q, prm, opt)                   # unjittered, [P, N, 3]
     tab = mlp.round_to(prm.table, "fp16" if arith == "bf16" else "fp32")
     feat = lambda f: mlp.round_to(f, "bf16" if arith == "bf16" else "fp32")
     f = feat(hashgrid.encode(x, tab, res, dense, fp32_grid=True))
@@ -168,8 +196,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # primary directions, slot 0 of sample q = gid * N + i
     q = np.asarray(global_ids, np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
-    u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
-    w_i = sampling.cosine_direction(n[:, None, :], u1, u2, _jitter(opt, global_ids, 0, (N, 3)))   # [P, N, 3]
+    w_i, wfac = _primary_dirs(x, n, wo, rough, q, prm, opt, _jitter(opt, global_ids, 0, (N, 3)))   # [P, N, 3]
 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
@@ -179,7 +206,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
         if opt.decision_arith == "fp64":
             v = (v > 0.5).to(v.dtype)
         else:
-            z0k, z2k = _kernel_logits(x, n, q, prm if decide is None else decide, opt, res, dense)
+            z0k, z2k = _kernel_logits(x, n, wo, rough, q, prm if decide is None else decide, opt, res, dense)
             v = (z0k.reshape(-1) > 0).to(v.dtype)
     if opt.force_vis >= 0:
         v = torch.full_like(v, opt.force_vis)
@@ -219,6 +246,8 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     li = v * le1 + (1.0 - v) * lo2
     fr1 = shading.brdf(albedo[:, None, :], rough[:, None], n[:, None, :], w_i, wo[:, None, :],
                        opt.f0, opt.lambert)
+    if wfac is not None:
+        fr1 = fr1 * wfac[..., None]
     out = shading.mc_sum(li * fr1, N)
     if opt.hard_vis and opt.flip_margin > 0:
         if z0k is None:

@@ -227,7 +227,7 @@ def test_kernel_logits_follow_the_float64_chain(arith, tol):
     dense = hashgrid.dense_levels(res, 1 << opt.log2_T, opt.dense_coarse)
     N, M = opt.n_dirs, opt.m_dirs
     q = rows.astype(np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
-    z0k, z2k = render._kernel_logits(x, n, q, prm, opt, res, dense)
+    z0k, z2k = render._kernel_logits(x, n, wo, rough, q, prm, opt, res, dense)
     # the float64 chain, written out from the oracle's stage functions
     u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
     w_i = sampling.cosine_direction(n[:, None, :], u1, u2)
