@@ -429,6 +429,20 @@ def run_ours(args, cfg):
         for r in rs:
             r.close()
 
+    # MIS primary directions (light + GGX visible normals, balance heuristic; Sec. 4.1)
+    mis_line = None
+    if not args.no_mis:
+        from paper_2409_10327_gb300 import binding
+        rs, gs = _setup(cfg, rank, sampling=binding.RT_SAMPLE_MIS)
+        steps = max(3, args.steps // 4)
+        m_total, m_launch, _ = _time_frames(rs, gs, out, steps, args.warmup, barrier)
+        m_total = max_over_ranks(m_total)
+        mis_line = {"sampling": "mis", "value": world * cfg.samples * steps / (m_total / 1e3), "unit": UNIT,
+                    "ms_per_frame": m_total / steps, "steps": steps,
+                    "kernel_ms": {"min": min(m_launch), "median": statistics.median(m_launch)}}
+        for r in rs:
+            r.close()
+
     # row a10: one distillation step (forward + hand-written adjoint)
     bwd = None if args.no_backward else time_backward(max(3, args.steps // 4), args.warmup, barrier)
 
@@ -453,7 +467,7 @@ def run_ours(args, cfg):
             "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "denoise": den, "backward": bwd,
+            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "mis": mis_line, "denoise": den, "backward": bwd,
             "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
                           "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
@@ -536,6 +550,7 @@ def main():
     ap.add_argument("--no-hard", action="store_true", help="skip the hard-visibility timing")
     ap.add_argument("--no-denoise", action="store_true", help="skip the denoiser timing")
     ap.add_argument("--no-backward", action="store_true", help="skip the backward (distillation step) timing")
+    ap.add_argument("--no-mis", action="store_true", help="skip the MIS-sampling timing")
     ap.add_argument("--mode", choices=["frame", "serve", "backward"], default="frame")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)

@@ -64,6 +64,7 @@ typedef enum rt_status {
 enum { RT_FP32 = 0, RT_BF16 = 1 };        /* precision                          */
 enum { RT_DISNEY = 0, RT_LAMBERT = 1 };   /* brdf_mode                          */
 enum { RT_VIS_SOFT = 0, RT_VIS_HARD = 1 }; /* visibility                         */
+enum { RT_SAMPLE_COSINE = 0, RT_SAMPLE_MIS = 1 }; /* sampling                    */
 
 /* Sizes and constants of one renderer instance.  Defaults: rt_config_default. */
 typedef struct rt_config {
@@ -89,6 +90,22 @@ typedef struct rt_config {
                             (a forced value counts as 1 above 0.5); only shadow
                             directions bounce and only visible secondary
                             directions count.  Render calls only.              */
+  int32_t sampling;      /* primary directions.  RT_SAMPLE_COSINE: cosine-weighted
+                            (header conventions).  RT_SAMPLE_MIS (Sec. 4.1):
+                            sample i is a light-importance draw for even i and a
+                            GGX visible-normal draw (Heitz 2018, alpha = r^2) for
+                            odd i (all light draws when n.w_o <= 1e-4), combined
+                            with the balance heuristic: each direction weighs
+                            f_r (n.w)+ L / (n_L p_L + n_G p_G).  The light draw
+                            inverts float32 CDFs of the map bound by rt_set_params
+                            (texel probability ~ max(0, luminance) + 1e-6, point
+                            uniform in (phi, theta) inside the texel) with (u1,
+                            u2).  Secondary directions stay cosine-weighted.
+                            Render calls only (rt_render_frame[_multi], rt_tune);
+                            rt_sample / rt_shade at level 0, rt_backward and
+                            rt_render_frame_static return RT_ERR_UNSUPPORTED.
+                            Multi-light renders draw from the bound map's
+                            distribution for every light (unbiased for each). */
   int32_t env_h, env_w;  /* environment map size, each 1..8192                  */
   uint64_t dir_seed;     /* SplitMix64 starting state of the direction sampler  */
 } rt_config;
@@ -147,7 +164,8 @@ rt_status rt_destroy(rt_ctx* ctx);
  * kept by reference), B and I blobs (float, layout of rt_param_count; copied
  * and repacked on `stream` into the context) and env [env_h][env_w][4] float
  * (rgb + ignored lane; kept by reference).  The table must be 8-byte
- * aligned.  Call again after the weights change.  Synchronises `stream`: the
+ * aligned.  Also builds the MIS texel CDFs of env (RT_SAMPLE_MIS) from its
+ * values at this call.  Call again after the weights or the map change.  Synchronises `stream`: the
  * FP32 biases and output layers are copied to the host once here, because
  * the BF16 kernel takes them as launch parameters. */
 rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, const float* irt_w,

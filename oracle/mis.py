@@ -115,6 +115,36 @@ def pdf_light(w: torch.Tensor, marg, cond) -> torch.Tensor:
     return p_t / ((2.0 * math.pi / W) * (math.pi / H) * sin_t)
 
 
+def pdf_light_neighbours(w: torch.Tensor, marg, cond, delta: float):
+    """Largest |p_L(w) - p_L'(w)| over the texels adjacent to w's own across a boundary that w lies
+    within `delta` radians of (0 elsewhere): the densities a kernel could use for w after rounding."""
+    H, W = cond.shape[0], cond.shape[1] - 1
+    x, y, z = w[..., 0], w[..., 1], w[..., 2]
+    theta = torch.acos(z.clamp(-1.0, 1.0))
+    phi = torch.atan2(y, x)
+    tq = theta / math.pi * H
+    tp = (phi + math.pi) / (2.0 * math.pi) * W
+    r = torch.clamp(torch.floor(tq).to(torch.int64), 0, H - 1)
+    c = torch.clamp(torch.floor(tp).to(torch.int64), 0, W - 1)
+    m = torch.from_numpy(marg.astype(np.float64))
+    cd = torch.from_numpy(cond.astype(np.float64))
+    sin_t = torch.sqrt(x * x + y * y)
+    scale = (2.0 * math.pi / W) * (math.pi / H) * sin_t
+
+    def p_at(rr, cc):
+        return (m[rr + 1] - m[rr]) * (cd[rr, cc + 1] - cd[rr, cc]) / scale
+    base = p_at(r, c)
+    worst = torch.zeros_like(base)
+    dq = delta * H / math.pi
+    dp = delta * W / (2.0 * math.pi)
+    for near, rr, cc in ((tq - r < dq, torch.clamp(r - 1, 0, H - 1), c),
+                         (r + 1 - tq < dq, torch.clamp(r + 1, 0, H - 1), c),
+                         (tp - c < dp, r, torch.remainder(c - 1, W)),
+                         (c + 1 - tp < dp, r, torch.remainder(c + 1, W))):
+        worst = torch.where(near, torch.maximum(worst, (p_at(rr, cc) - base).abs()), worst)
+    return worst
+
+
 def frame(n: torch.Tensor):
     """Orthonormal (t, b) completing the unit normal n (Duff et al. 2017)."""
     sign = torch.where(n[..., 2] >= 0, torch.ones_like(n[..., 2]), -torch.ones_like(n[..., 2]))

@@ -72,6 +72,7 @@ class Options:
     sampling: str = "cosine"     # primary directions: 'cosine' or 'mis' (light + GGX, balance heuristic; mis.py)
     decision_arith: str = "fp64"  # arithmetic of the hard decisions: 'fp64', 'fp32' or 'bf16'
     flip_margin: float = 0.0     # > 0: also return the flip allowance of rows with |z0| < margin
+    mis_margin: float = 0.0      # > 0 (MIS): also return the allowance of directions within this angle of a texel edge
     dir_seed: int = 0x5EED
     dense_coarse: bool = True
     # conditioning probe: relative Gaussian jitter of the secondary points x'
@@ -121,16 +122,27 @@ def _primary_dirs(x, n, wo, rough, q, prm: Params, opt: Options, jitter=None):
 
     Cosine sampling: the weight is None ((w . n) / p = pi).  MIS: the factor
     (n . w)+ / (n_L p_L + n_G p_G) times N / pi, so that (pi / N) sum stays the
-    estimator's form.  `jitter` [P, N, 3] (conditioning probe only) is added to
+    estimator's form.  With opt.mis_margin > 0 also returns how far that factor
+    can move when p_L is read from a texel next to the direction's own (for
+    directions within the margin of a texel edge), else None.  `jitter` [P, N, 3] (conditioning probe only) is added to
     the sphere point of a cosine sample or to an MIS direction.
     """
     N, M = opt.n_dirs, opt.m_dirs
     u1, u2 = sampling.uniforms(opt.dir_seed, sampling.counters(q, 0, M))
     if opt.sampling == "cosine":
-        return sampling.cosine_direction(n[:, None, :], u1, u2, jitter), None
+        return sampling.cosine_direction(n[:, None, :], u1, u2, jitter), None, None
     marg, cond = mis.env_cdf(prm.env.detach().numpy()[..., :3].astype(np.float32))
     w, fac = mis.primary_directions(n, wo, rough, u1, u2, N, marg, cond)
     if jitter is not None:
+        # the GGX visible-normal map amplifies the rounding of its own arithmetic near the
+        # rim of its disk, so the probe also moves the uniforms of GGX draws (their map is
+        # continuous; the light draws' CDF inversion is a decision both sides take alike)
+        g_rows = ((n * wo).sum(-1) > mis.NOV_MIN)[:, None] & torch.from_numpy((np.arange(N) % 2 == 1)[None, :])
+        lim = 1.0 - 2.0 ** -24
+        w_g = mis.sample_ggx(n[:, None, :].expand_as(w), wo[:, None, :].expand_as(w),
+                             (rough * rough)[:, None].expand(w.shape[:2]),
+                             (u1 + jitter[..., 0]).clamp(0.0, lim), (u2 + jitter[..., 1]).clamp(0.0, lim))
+        w = torch.where(g_rows[..., None], w_g, w)
         w = w + jitter
         w = w / w.norm(dim=-1, keepdim=True)
         nv = n[:, None, :].expand_as(w)
@@ -140,7 +152,19 @@ def _primary_dirs(x, n, wo, rough, q, prm: Params, opt: Options, jitter=None):
                           torch.zeros_like(rough))[:, None]
         den = (N - n_g) * mis.pdf_light(w, marg, cond) + n_g * mis.pdf_ggx(w, nv, wv, alpha)
         fac = torch.clamp((nv * w).sum(-1), min=0.0) / den
-    return w, fac * (N / math.pi)
+    dfac = None
+    if opt.mis_margin > 0:
+        nv = n[:, None, :].expand_as(w)
+        wv = wo[:, None, :].expand_as(w)
+        alpha = (rough * rough)[:, None].expand(w.shape[:2])
+        n_g = torch.where((n * wo).sum(-1) > mis.NOV_MIN, torch.full_like(rough, N // 2),
+                          torch.zeros_like(rough))[:, None]
+        den = (N - n_g) * mis.pdf_light(w, marg, cond) + n_g * mis.pdf_ggx(w, nv, wv, alpha)
+        dp = (N - n_g) * mis.pdf_light_neighbours(w, marg, cond, opt.mis_margin)
+        cos = torch.clamp((nv * w).sum(-1), min=0.0)
+        # |cos / (den - dp) - cos / den| bounds the change when the density moves by at most dp
+        dfac = cos * dp / (den * torch.clamp(den - dp, min=1e-300)) * (N / math.pi)
+    return w, fac * (N / math.pi), dfac
 
 
 def _kernel_logits(x, n, wo, rough, q, prm: Params, opt: Options, res, dense):
@@ -154,7 +178,7 @@ def _kernel_logits(x, n, wo, rough, q, prm: Params, opt: Options, res, dense):
     """
     arith = opt.decision_arith
     P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
-    w_i, _ = _primary_dirs(x, n, wo, rough, q, prm, opt)                   # unjittered, [P, N, 3]
+    w_i, _, _ = _primary_dirs(x, n, wo, rough, q, prm, opt)                # unjittered, [P, N, 3]
     tab = mlp.round_to(prm.table, "fp16" if arith == "bf16" else "fp32")
     feat = lambda f: mlp.round_to(f, "bf16" if arith == "bf16" else "fp32")
     f = feat(hashgrid.encode(x, tab, res, dense, fp32_grid=True))
@@ -196,7 +220,7 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
 
     # primary directions, slot 0 of sample q = gid * N + i
     q = np.asarray(global_ids, np.uint64)[:, None] * np.uint64(N) + np.arange(N, dtype=np.uint64)[None, :]
-    w_i, wfac = _primary_dirs(x, n, wo, rough, q, prm, opt, _jitter(opt, global_ids, 0, (N, 3)))   # [P, N, 3]
+    w_i, wfac, dfac = _primary_dirs(x, n, wo, rough, q, prm, opt, _jitter(opt, global_ids, 0, (N, 3)))  # [P, N, 3]
 
     # (c) visibility and depth along w_i
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
@@ -246,9 +270,13 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
     li = v * le1 + (1.0 - v) * lo2
     fr1 = shading.brdf(albedo[:, None, :], rough[:, None], n[:, None, :], w_i, wo[:, None, :],
                        opt.f0, opt.lambert)
+    base_term = li * fr1
     if wfac is not None:
         fr1 = fr1 * wfac[..., None]
     out = shading.mc_sum(li * fr1, N)
+    allow_mis = None
+    if dfac is not None:
+        allow_mis = shading.mc_sum(base_term.abs() * dfac[..., None], N)
     if opt.hard_vis and opt.flip_margin > 0:
         if z0k is None:
             raise ValueError("flip_margin needs a kernel decision_arith")
@@ -263,7 +291,11 @@ def render_points(x, n, wo, albedo, rough, global_ids: np.ndarray, prm: Params, 
         d_sec = shading.mc_sum(amb2 * (le2 * fr2).abs(), M).reshape(P, N, 3)
         reach = torch.maximum(1.0 - v, amb1)
         allow = shading.mc_sum((amb1 * (le1 - lo2).abs() + reach * d_sec) * fr1.abs(), N)
+        if allow_mis is not None:
+            allow = allow + allow_mis
         return out, allow
+    if allow_mis is not None:
+        return out, allow_mis
     if want_dirs:
         return out, w_j.detach()
     return out
@@ -292,7 +324,7 @@ def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: i
     P = gb["pos"].shape[0]
     rows = np.arange(P) if rows is None else np.asarray(rows)
     per = max(1, chunk_rows // (opt.n_dirs * opt.m_dirs))
-    pair = opt.hard_vis and opt.flip_margin > 0
+    pair = (opt.hard_vis and opt.flip_margin > 0) or (opt.sampling == "mis" and opt.mis_margin > 0)
     out, allow = [], []
     with torch.no_grad():
         for s in range(0, rows.size, per):
@@ -309,7 +341,7 @@ def render(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: i
 
 def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pixel_offset: int = 0,
                         rows: Optional[np.ndarray] = None, rel: float = 2.0 ** -23, draws: int = 2,
-                        mlp: bool = False) -> np.ndarray:
+                        mlp: bool = False, table_rel: float = 2.0 ** -11) -> np.ndarray:
     """Per-pixel, per-channel max |L(jittered) - L| over `draws` float32-sized jitters.
 
     Two inputs of the exact result are ill-conditioned at float32 scale:
@@ -322,23 +354,24 @@ def float32_sensitivity(gb: Dict[str, np.ndarray], prm: Params, opt: Options, pi
     and reports how far the exact result moves; the FP32 parity tests scale
     their per-pixel bound by it.  With mlp=True it also jitters the MLP inputs
     and hidden activations (per sample) and both hidden weight matrices (per
-    draw) by `rel`, and the table by 2^-11: the roundings of a bf16 MLP with
-    an FP16 table, used by the BF16 tests.
+    draw) by `rel`, and the table by `table_rel` (2^-11: the roundings of a
+    bf16 MLP with an FP16 table, used by the BF16 tests; 0 for a float32
+    table, which both sides read exactly).
     """
-    opt = dataclasses.replace(opt, flip_margin=0.0)
+    opt = dataclasses.replace(opt, flip_margin=0.0, mis_margin=0.0)
     decide = prm if (opt.hard_vis and opt.decision_arith != "fp64") else None   # decisions stay those of base
     base = render(gb, prm, opt, pixel_offset, rows)
     worst = np.zeros_like(base)
     for d in range(draws):
         o = dataclasses.replace(opt, x2_jitter=rel, s_jitter=rel, mlp_jitter=rel if mlp else 0.0, jitter_seed=1 + d)
-        p = _perturbed_weights(prm, rel, 1 + d) if mlp else prm
+        p = _perturbed_weights(prm, rel, 1 + d, table_rel) if mlp else prm
         worst = np.maximum(worst, np.abs(render(gb, p, o, pixel_offset, rows, decide=decide) - base))
     return worst
 
 
-def _perturbed_weights(prm: Params, rel: float, seed: int) -> Params:
+def _perturbed_weights(prm: Params, rel: float, seed: int, table_rel: float = 2.0 ** -11) -> Params:
     """Params with both hidden layers' weight matrices scaled by (1 + rel z) and the
-    table by (1 + 2^-11 z): the systematic part of bf16 weights and an FP16 table."""
+    table by (1 + table_rel z): the systematic part of bf16 weights and an FP16 table."""
     g = torch.Generator().manual_seed(seed)
 
     def jw(layers):
@@ -348,7 +381,7 @@ def _perturbed_weights(prm: Params, rel: float, seed: int) -> Params:
                 w = w * (1.0 + rel * torch.randn(w.shape, generator=g, dtype=w.dtype))
             out.append((w, b))
         return out
-    table = prm.table * (1.0 + 2.0 ** -11 * torch.randn(prm.table.shape, generator=g, dtype=prm.table.dtype))
+    table = prm.table * (1.0 + table_rel * torch.randn(prm.table.shape, generator=g, dtype=prm.table.dtype))
     return Params(table, jw(prm.brdf), jw(prm.irt), prm.env)
 
 

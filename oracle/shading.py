@@ -69,7 +69,7 @@ def env_lookup(env: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
 
 
 def ggx_d(noh: torch.Tensor, a2: torch.Tensor) -> torch.Tensor:
-    """GGX normal distribution with alpha^2 = a2."""
+    """GGX normal distribution with alpha^2 = a2 (unit vectors; brdf() uses the |n x h|^2 form)."""
     return a2 / (math.pi * (noh * noh * (a2 - 1.0) + 1.0) ** 2)
 
 
@@ -102,9 +102,16 @@ def brdf(albedo: torch.Tensor, rough: torch.Tensor, n: torch.Tensor, wi: torch.T
     hl2 = (hv * hv).sum(-1)
     ok = hl2 > 1e-20
     hl = torch.sqrt(torch.where(ok, hl2, torch.ones_like(hl2)))
-    noh = torch.where(ok, (n * hv).sum(-1) / hl, torch.zeros_like(hl)).clamp(min=0.0)
+    h = hv / hl[..., None]
+    noh_raw = torch.where(ok, (n * h).sum(-1), torch.zeros_like(hl))
+    noh = noh_raw.clamp(min=0.0)
     voh = torch.where(ok, 0.5 * hl, torch.zeros_like(hl))
-    spec = ggx_d(noh, a2) * schlick_fresnel(voh, f0) * smith_vis(nol, nov, a2)
+    # GGX D with 1 - (n.h)^2 written as |n x h|^2 (equal for unit vectors; the same
+    # expression as the GGX sampling density, so that D cancels between the two
+    # on inputs that are unit only to float32 rounding); D = a2 / pi where n.h <= 0
+    c = torch.cross(n.expand_as(h), h, dim=-1)
+    dd = torch.where(ok & (noh_raw > 0), (c * c).sum(-1) + noh * noh * a2, torch.ones_like(hl))
+    spec = a2 / (math.pi * dd * dd) * schlick_fresnel(voh, f0) * smith_vis(nol, nov, a2)
     return diffuse + spec[..., None]
 
 

@@ -22,6 +22,7 @@ RT_OK, RT_ERR_INVALID_ARG, RT_ERR_UNSUPPORTED, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_T
 RT_FP32, RT_BF16 = 0, 1
 RT_DISNEY, RT_LAMBERT = 0, 1
 RT_VIS_SOFT, RT_VIS_HARD = 0, 1
+RT_SAMPLE_COSINE, RT_SAMPLE_MIS = 0, 1
 
 # Every symbol include/rt.h declares.
 EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level_resolution",
@@ -37,7 +38,8 @@ class RtConfig(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("n_dirs", ctypes.c_int32), ("m_dirs", ctypes.c_int32),
                 ("brdf_mode", ctypes.c_int32), ("near_t", ctypes.c_float), ("far_t", ctypes.c_float),
                 ("f0", ctypes.c_float), ("force_vis", ctypes.c_float), ("force_vis2", ctypes.c_float),
-                ("visibility", ctypes.c_int32), ("env_h", ctypes.c_int32), ("env_w", ctypes.c_int32),
+                ("visibility", ctypes.c_int32), ("sampling", ctypes.c_int32), ("env_h", ctypes.c_int32),
+                ("env_w", ctypes.c_int32),
                 ("dir_seed", ctypes.c_uint64)]
 
 

@@ -18,6 +18,7 @@ struct rt_ctx {
   float* wpack;        // WPACK_FLOATS
   uint8_t* wbf16;      // WBF16_BYTES
   uint32_t* status;    // device status word
+  float* cdf;          // MIS texel CDFs: marginal [env_h + 1], then conditional [env_h][env_w + 1]
   const void* table;
   const float* env;
   HeadParams head;     // host copy of the FP32 output layers (BF16 kernel parameter)
@@ -43,6 +44,8 @@ bool level_dense(const rt_config* c, int res) {
   const double n1 = (double)res + 1.0;
   return n1 * n1 * n1 <= (double)(1LL << c->log2_T);
 }
+
+int64_t cdf_floats(const rt_config& c) { return (int64_t)(c.env_h + 1) + (int64_t)c.env_h * (c.env_w + 1); }
 
 ModelDesc model_desc(const rt_ctx* ctx) {
   ModelDesc m{};
@@ -72,6 +75,9 @@ ModelDesc model_desc(const rt_ctx* ctx) {
   m.force_vis = c.force_vis;
   m.force_vis2 = c.force_vis2;
   m.hard = c.visibility == RT_VIS_HARD ? 1 : 0;
+  m.mis = c.sampling == RT_SAMPLE_MIS ? 1 : 0;
+  m.cdf_m = ctx->cdf;
+  m.cdf_c = ctx->cdf + (c.env_h + 1);
   m.lambert = c.brdf_mode == RT_LAMBERT;
   m.seed = c.dir_seed;
   return m;
@@ -128,6 +134,7 @@ rt_status rt_config_default(rt_config* c) {
   c->force_vis = -1.0f;
   c->force_vis2 = -1.0f;
   c->visibility = RT_VIS_SOFT;
+  c->sampling = RT_SAMPLE_COSINE;
   c->env_h = 64;
   c->env_w = 128;
   c->dir_seed = 0x5EED;
@@ -145,6 +152,7 @@ rt_status rt_config_validate(const rt_config* c) {
                   c->far_t > c->near_t && std::isfinite(c->f0) && c->f0 >= 0.0f && c->f0 <= 1.0f &&
                   !std::isnan(c->force_vis) && c->force_vis <= 1.0f && !std::isnan(c->force_vis2) &&
                   c->force_vis2 <= 1.0f && (c->visibility == RT_VIS_SOFT || c->visibility == RT_VIS_HARD) &&
+                  (c->sampling == RT_SAMPLE_COSINE || c->sampling == RT_SAMPLE_MIS) &&
                   c->env_h >= 1 && c->env_h <= 8192 && c->env_w >= 1 &&
                   c->env_w <= 8192;
   return ok ? RT_OK : RT_ERR_INVALID_ARG;
@@ -174,10 +182,11 @@ int64_t rt_param_count(const rt_config* c, int32_t which) {
 
 int64_t rt_workspace_bytes(const rt_config* c) {
   if (rt_config_validate(c) != RT_OK) return -1;
-  return (int64_t)WPACK_FLOATS * 4 + WBF16_BYTES + 256;
+  return (int64_t)WPACK_FLOATS * 4 + WBF16_BYTES + 256 + cdf_floats(*c) * 4;
 }
 
 rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
+  // (the MIS texel CDFs are allocated with the rest of the workspace, whatever the sampling mode)
   if (out == nullptr) return RT_ERR_INVALID_ARG;
   *out = nullptr;
   if (rt_config_validate(cfg) != RT_OK) return RT_ERR_INVALID_ARG;
@@ -210,11 +219,19 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
     delete ctx;
     return RT_ERR_OOM;
   }
+  if (cudaMalloc(&ctx->cdf, (size_t)cdf_floats(*cfg) * 4) != cudaSuccess) {
+    cudaFree(ctx->wpack);
+    cudaFree(ctx->wbf16);
+    cudaFree(ctx->status);
+    delete ctx;
+    return RT_ERR_OOM;
+  }
   cudaError_t e = rtk::prepare_kernels();
   if (e != cudaSuccess) {
     cudaFree(ctx->wpack);
     cudaFree(ctx->wbf16);
     cudaFree(ctx->status);
+    cudaFree(ctx->cdf);
     delete ctx;
     return RT_ERR_CUDA;
   }
@@ -228,6 +245,7 @@ rt_status rt_destroy(rt_ctx* ctx) {
   cudaFree(ctx->wpack);
   cudaFree(ctx->wbf16);
   cudaFree(ctx->status);
+  cudaFree(ctx->cdf);
   delete ctx;
   return cuda_status(e);
 }
@@ -244,6 +262,9 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
   const int lf = ctx->cfg.levels * ctx->cfg.feat_dim;
   cudaStream_t s = (cudaStream_t)stream;
   rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, s));
+  if (st == RT_OK)
+    st = cuda_status(launch_env_cdf(reinterpret_cast<const float4*>(env), ctx->cfg.env_h, ctx->cfg.env_w, ctx->cdf,
+                                    ctx->cdf + (ctx->cfg.env_h + 1), s));
   if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, s));
   if (st != RT_OK) return st;
   // host copy of the output layers for the BF16 kernel's parameters
@@ -316,6 +337,7 @@ rt_status rt_sample(rt_ctx* ctx, const float* normal, int64_t P, int32_t level, 
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
   if (P < 0 || P > kMaxP || (level != 0 && level != 1) || index_offset < 0) return RT_ERR_INVALID_ARG;
+  if (level == 0 && ctx->cfg.sampling == RT_SAMPLE_MIS) return RT_ERR_UNSUPPORTED;
   if (P == 0) return RT_OK;
   if (!check_plane(normal) || !check_plane(dirs)) return RT_ERR_INVALID_ARG;
   return cuda_status(launch_sample(model_desc(ctx), reinterpret_cast<const float4*>(normal), (int)P, level,
@@ -327,6 +349,7 @@ rt_status rt_shade(rt_ctx* ctx, const rt_gbuffer* pts, int64_t P, int32_t level,
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
   if (P < 0 || P > kMaxP || (level != 0 && level != 1) || index_offset < 0) return RT_ERR_INVALID_ARG;
+  if (level == 0 && ctx->cfg.sampling == RT_SAMPLE_MIS) return RT_ERR_UNSUPPORTED;
   if (P == 0) return RT_OK;
   if (pts == nullptr || !check_plane(pts->normal) || !check_plane(pts->view) || !check_plane(pts->albedo_rough) ||
       vis == nullptr || !aligned(vis, 4) || (lin != nullptr && (level == 1 || !aligned(lin, 16))) ||
@@ -456,7 +479,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
   if (P < 0 || P > kMaxP || pixel_offset < 0) return RT_ERR_INVALID_ARG;
-  if (ctx->cfg.visibility == RT_VIS_HARD) return RT_ERR_UNSUPPORTED;
+  if (ctx->cfg.visibility == RT_VIS_HARD || ctx->cfg.sampling == RT_SAMPLE_MIS) return RT_ERR_UNSUPPORTED;
   if (P == 0) return RT_OK;
   if (!check_gbuffer(gb) || !check_plane(d_radiance) || g_table == nullptr || !aligned(g_table, 8) ||
       g_brdf == nullptr || !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))

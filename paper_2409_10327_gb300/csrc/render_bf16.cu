@@ -31,6 +31,7 @@
 
 #include "device_common.cuh"
 #include "fast_math.cuh"
+#include "mis.cuh"
 
 namespace rtk {
 
@@ -597,7 +598,9 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
       const f3 wo = xyz(view4[p]);
       const float4 ar = ar4[p];
       const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)pi.y;
-      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      // MIS: the direction's Eq. 1 weight relative to cosine sampling rides on fr1
+      const f3 fr1 = m.mis ? mis_weighted_brdf(m, xyz(ar), ar.w, n, wo, wi)
+                           : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       // (d) x' = x + t w_i and f' = H(x'); (b) B(f')
       encode_point_tmem(m.grid, x + wi * qw.w, X_w);
       if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) return false;
@@ -662,9 +665,12 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
       const f3 wo = xyz(view4[p]);
       const float4 ar = ar4[p];
       const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
-      const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
+      const f3 wi = m.mis ? mis_direction(m, n, wo, ar.w, i, dir_counter(q, M, 0))
+                          : cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
       const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
-      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      // MIS: the direction's Eq. 1 weight relative to cosine sampling rides on fr1
+      const f3 fr1 = m.mis ? mis_weighted_brdf(m, xyz(ar), ar.w, n, wo, wi)
+                           : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       {
         const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
         uint32_t fr[16];
@@ -762,11 +768,14 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
       const f3 wo = xyz(view4[p]);
       const float4 ar = ar4[p];
       const uint64_t q = (uint64_t)(pixel_offset + p) * (uint64_t)N + (uint64_t)i;
-      const f3 wi = cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
+      const f3 wi = m.mis ? mis_direction(m, n, wo, ar.w, i, dir_counter(q, M, 0))
+                          : cosine_direction_fast(n, m.seed, dir_counter(q, M, 0));
       // Eq. 1 factors of the primary direction, fetched before the MMAs so the
       // env-map loads overlap them
       const EnvTap tap1 = env_tap_fast(m.env_h, m.env_w, wi);
-      const f3 fr1 = brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      // MIS: the direction's Eq. 1 weight relative to cosine sampling rides on fr1
+      const f3 fr1 = m.mis ? mis_weighted_brdf(m, xyz(ar), ar.w, n, wo, wi)
+                           : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       f3 le1 = mk(0.f, 0.f, 0.f);
       if (NL == 1) le1 = env_fetch(envs, tap1);
       {

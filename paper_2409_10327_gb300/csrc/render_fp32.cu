@@ -10,6 +10,7 @@
 // the GEMM operand reads are broadcasts and the epilogue stores are free of
 // bank conflicts.  The per-point reductions over directions are warp
 // shuffles; nothing but the radiance is written to global memory.
+#include "mis.cuh"
 #include "warp_gemm.cuh"
 
 namespace rtk {
@@ -93,7 +94,9 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
     for (int i0 = 0; i0 < N; i0 += 32) {
       const int i = i0 + lane;
       const uint64_t q = (uint64_t)(pixel_offset + pix) * (uint64_t)N + (uint64_t)i;
-      const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+      // primary direction (MIS: its Eq. 1 weight relative to cosine sampling rides on the BRDF below)
+      const f3 wi = m.mis ? mis_direction(m, n, wo, ar.w, i, dir_counter(q, M, 0))
+                          : cosine_direction(n, m.seed, dir_counter(q, M, 0));
 
       // (c) I(f, w_i)
       float acc[8][8];
@@ -185,7 +188,8 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
 
       // Eq. 2 then the primary term of Eq. 1
       const f3 li = env_lookup(m.env, m.env_h, m.env_w, wi) * v + lo2 * (1.0f - v);
-      const f3 c = li * brdf_eval(alb, ar.w, n, wi, wo, m.f0, m.lambert);
+      const f3 c = li * (m.mis ? mis_weighted_brdf(m, alb, ar.w, n, wo, wi)
+                               : brdf_eval(alb, ar.w, n, wi, wo, m.f0, m.lambert));
       if (i < N) sum = sum + c;
     }
 #pragma unroll

@@ -86,6 +86,9 @@ struct ModelDesc {
   float near_t, far_t, f0;
   float force_vis, force_vis2;
   int hard;                    // 1: hard visibility (RT_VIS_HARD)
+  int mis;                     // 1: MIS primary directions (RT_SAMPLE_MIS)
+  const float* cdf_m;          // [env_h + 1] marginal CDF of the bound map's texel distribution
+  const float* cdf_c;          // [env_h][env_w + 1] conditional CDFs
   int lambert;
   uint64_t seed;
 };
@@ -127,6 +130,7 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                float4* out, int num_sms, cudaStream_t s);
+cudaError_t launch_env_cdf(const float4* env, int H, int W, float* cdf_m, float* cdf_c, cudaStream_t s);
 cudaError_t launch_denoise(int W, int H, const float4* rad, const float* z, const float4* nrm, int iterations,
                            float sigma_z, float sigma_n, float sigma_l, float4* work, float4* out, cudaStream_t s);
 cudaError_t launch_backward_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,

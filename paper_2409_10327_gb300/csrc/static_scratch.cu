@@ -67,7 +67,7 @@ extern "C" rt_status rt_render_frame_static(const rt_config* cfg, const void* ta
                                             const float* irt_w, const float* env, const rt_gbuffer* gb, int64_t P,
                                             int64_t pixel_offset, float* radiance, void* stream) {
   if (rt_config_validate(cfg) != RT_OK) return RT_ERR_INVALID_ARG;
-  if (cfg->precision != RT_FP32) return RT_ERR_UNSUPPORTED;
+  if (cfg->precision != RT_FP32 || cfg->sampling == RT_SAMPLE_MIS) return RT_ERR_UNSUPPORTED;
   // The static array holds exactly one packed image: 2 x L features per point
   // must fit its 32 feature rows (always true for a valid config, L <= 16).
   if (cfg->levels * cfg->feat_dim > 32) return RT_ERR_INVALID_ARG;
@@ -108,6 +108,7 @@ extern "C" rt_status rt_render_frame_static(const rt_config* cfg, const void* ta
   m.force_vis = cfg->force_vis;
   m.force_vis2 = cfg->force_vis2;
   m.hard = cfg->visibility == RT_VIS_HARD ? 1 : 0;
+  m.mis = 0;   // MIS needs the texel CDFs of a context: rejected above
   m.lambert = cfg->brdf_mode == RT_LAMBERT;
   m.seed = cfg->dir_seed;
 

@@ -142,3 +142,19 @@ def test_mis_matches_the_direct_light_integral():
         cos = torch.clamp((w * n).sum(-1), min=0.0)
         ref = ((fr * le * cos[..., None]).numpy() * dA[..., None]).sum((0, 1))
         np.testing.assert_allclose(out[p], ref, rtol=0.03)
+
+
+def test_texel_edge_allowance_is_the_neighbouring_density():
+    # a direction just inside a column edge: the allowance is |p_L(next texel) - p_L(own texel)|;
+    # away from every edge it is 0
+    marg, cond = mis.env_cdf(_env(6, 10, 5))
+    th = math.pi * 2.5 / 6                       # mid-row 2
+    def d(phi):
+        return torch.tensor([[math.sin(th) * math.cos(phi), math.sin(th) * math.sin(phi), math.cos(th)]],
+                            dtype=torch.float64)
+    edge = 2.0 * math.pi * 4 / 10 - math.pi      # left edge of column 4
+    w_in, w_out = d(edge + 1e-7), d(edge - 1e-7)
+    got = mis.pdf_light_neighbours(w_in, marg, cond, 1e-6)
+    ref = (mis.pdf_light(w_out, marg, cond) - mis.pdf_light(w_in, marg, cond)).abs()
+    assert float(got) == pytest.approx(float(ref), rel=1e-6)
+    assert float(mis.pdf_light_neighbours(d(edge + 0.1), marg, cond, 1e-6)) == 0.0
