@@ -321,6 +321,50 @@ def time_backward(steps: int, warmup: int, barrier, rays: int = 0):
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}}
 
 
+def time_distill(steps: int, warmup: int, barrier, rays: int = 2048, K: int = 1024):
+    """One online per-head distillation step (Sec. 3.3; supplementary "Training Details": 2,048 rays x
+    1,024 stratified directions): directions, the teacher's heads, the student's adjoint, Adam on the
+    table and both MLPs, and the rebinding of the student (which synchronises)."""
+    import dataclasses
+    import torch
+    from paper_2409_10327_gb300 import binding, distill
+    cfg = dataclasses.replace(scenegen.CONFIGS["grad65k"], width=rays, height=1)
+
+    def renderer(seed):
+        sc = scenegen.make_scene(cfg, seed, bias_scale=0.1)
+        r = binding.Renderer(binding.make_config(cfg))
+        r.set_params(torch.from_numpy(sc.table).cuda(), torch.from_numpy(sc.brdf_blob).cuda(),
+                     torch.from_numpy(sc.irt_blob).cuda(), torch.from_numpy(sc.env).cuda())
+        return r, sc
+    teacher, _ = renderer(1)
+    student, sc = renderer(2)
+    d = distill.Distiller(student, teacher, torch.from_numpy(sc.table).cuda(), torch.from_numpy(sc.brdf_blob).cuda(),
+                          torch.from_numpy(sc.irt_blob).cuda(), torch.from_numpy(sc.env).cuda(), K=K)
+    gb = scenegen.make_gbuffer(rays, 9)
+    pos = torch.from_numpy(gb["pos"]).cuda()
+    nrm = torch.from_numpy(gb["normal"]).cuda()
+    first = None
+    for w in range(warmup):
+        loss = d.step(pos, nrm, ray_offset=w * rays)
+        if first is None:
+            first = float(loss.sum())
+    barrier()
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        loss = d.step(pos, nrm, ray_offset=(warmup + k) * rays)
+    t1.record(stream)
+    barrier()
+    ms = t0.elapsed_time(t1) / steps
+    out = {"workload": f"{rays} rays x {K} stratified directions, L=16, T=2^19, fp32 student and teacher",
+           "ms_per_step": ms, "value": rays * K / (ms / 1e3), "unit": "ray-direction pairs/s", "steps": steps,
+           "loss_first_last": [first, float(loss.sum())]}
+    teacher.close()
+    student.close()
+    return out
+
+
 def run_ours(args, cfg):
     import dataclasses
     import torch
@@ -445,6 +489,7 @@ def run_ours(args, cfg):
 
     # row a10: one distillation step (forward + hand-written adjoint)
     bwd = None if args.no_backward else time_backward(max(3, args.steps // 4), args.warmup, barrier)
+    dst = None if args.no_distill else time_distill(max(3, args.steps // 4), args.warmup, barrier)
 
     if rank != 0:
         if world > 1:
@@ -467,7 +512,7 @@ def run_ours(args, cfg):
             "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "mis": mis_line, "denoise": den, "backward": bwd,
+            "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "mis": mis_line, "denoise": den, "backward": bwd, "distill": dst,
             "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms),
                           "all": [round(x, 3) for x in launch_ms]}}
     print(json.dumps(line))
@@ -551,6 +596,7 @@ def main():
     ap.add_argument("--no-denoise", action="store_true", help="skip the denoiser timing")
     ap.add_argument("--no-backward", action="store_true", help="skip the backward (distillation step) timing")
     ap.add_argument("--no-mis", action="store_true", help="skip the MIS-sampling timing")
+    ap.add_argument("--no-distill", action="store_true", help="skip the distillation-step timing")
     ap.add_argument("--mode", choices=["frame", "serve", "backward"], default="frame")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)

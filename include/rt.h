@@ -297,6 +297,41 @@ rt_status rt_render_frame_static(const rt_config* cfg, const void* table, const 
                                  const float* env, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                                  float* radiance, void* stream);
 
+/* ---- per-head distillation (Sec. 3.3, supplementary "Training Details") -- */
+
+/* K stratified directions on the whole sphere for each of P points: K = S^2
+ * cells of the unit square, direction k of point p from cell (k / S, k % S)
+ * plus the uniforms of counter (ray_offset + p) * K + k (header
+ * conventions' SplitMix64, seed cfg.dir_seed), mapped by z = 1 - 2 u1,
+ * azimuth 2 pi u2.  dirs [P][K][4] float (xyz, 0), device, 16-byte aligned.
+ * K must be a perfect square (1..65536); P * K < 2^31. */
+rt_status rt_distill_dirs(rt_ctx* ctx, int64_t P, int32_t K, int64_t ray_offset, float* dirs, void* stream);
+
+/* ACCUMULATES the gradient of the per-head distillation loss of the student
+ * ctx (RT_FP32 only, else RT_ERR_UNSUPPORTED) into g_table [L][T][F],
+ * g_brdf and g_irt (float, blob layouts; the caller zeroes them), and adds
+ * the three loss terms to loss[0..2] (float, may be NULL):
+ *   loss[0] = mean over points and the 7 components of |B's (n', a', r') -
+ *             brdf_t| (L1 after n/|n|, sigmoid and 0.09 + 0.91 sigmoid);
+ *   loss[1] = mean over points of the mean over the point's front-facing
+ *             directions (w . n > 0) of BCE(sigmoid(z0), v_t), v_t =
+ *             1 when vis_t > 0.5 (the teacher's visibility binarised);
+ *   loss[2] = the same mean of |min(softplus(z1), 1) - (depth_t - near) /
+ *             (far - near)| (min-max normalised depth).
+ * pos, normal [P][4] (xyz used), dirs [P][K][4] (rt_distill_dirs); brdf_t
+ * [P][8] (n', a', r', pad: a teacher's rt_decode), vis_t, depth_t [P][K]
+ * (a teacher's rt_trace on dirs).  Sampled directions are constants. */
+rt_status rt_distill_backward(rt_ctx* ctx, const float* pos, const float* normal, int64_t P, int32_t K,
+                              const float* dirs, const float* brdf_t, const float* vis_t, const float* depth_t,
+                              float* loss, float* g_table, float* g_brdf, float* g_irt, void* stream);
+
+/* One Adam step in place over n floats (device): g' = grad + weight_decay *
+ * param (L2 form), m1 = beta1 m1 + (1 - beta1) g', m2 = beta2 m2 + (1 -
+ * beta2) g'^2, param -= lr (m1 / (1 - beta1^step)) / (sqrt(m2 / (1 -
+ * beta2^step)) + eps).  step >= 1.  Needs no context. */
+rt_status rt_adam_step(float* param, const float* grad, float* m1, float* m2, int64_t n, float lr, float beta1,
+                       float beta2, float eps, float weight_decay, int32_t step, void* stream);
+
 /* ---- denoising --------------------------------------------------------- */
 
 /* Spatial SVGF (Schied et al. 2017) with its temporal parts removed, as the

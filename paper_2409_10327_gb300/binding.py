@@ -29,7 +29,8 @@ EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level
            "rt_level_is_dense", "rt_param_count", "rt_workspace_bytes", "rt_create", "rt_destroy",
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
            "rt_render_frame", "rt_backward", "rt_render_frame_static", "rt_render_frame_multi", "rt_tune",
-           "rt_tuned_shape", "rt_set_launch_shape", "rt_denoise"]
+           "rt_tuned_shape", "rt_set_launch_shape", "rt_denoise", "rt_distill_dirs",
+           "rt_distill_backward", "rt_adam_step"]
 
 
 class RtConfig(ctypes.Structure):
@@ -85,6 +86,9 @@ def _load() -> ctypes.CDLL:
         "rt_tuned_shape": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "rt_set_launch_shape": (I32, [P, I32, I32]),
         "rt_denoise": (I32, [I32, I32, P, P, P, I32, F32, F32, F32, P, P, P]),
+        "rt_distill_dirs": (I32, [P, I64, I32, I64, P, P]),
+        "rt_distill_backward": (I32, [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P]),
+        "rt_adam_step": (I32, [P, P, P, P, I64, F32, F32, F32, F32, F32, I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +166,14 @@ def denoise(radiance: torch.Tensor, depth: torch.Tensor, normal: torch.Tensor, w
     _check("rt_denoise", LIB.rt_denoise(width, height, _ptr(radiance), _ptr(depth), _ptr(normal), iterations,
                                         sigma_z, sigma_n, sigma_l, _ptr(work), _ptr(out), _stream()))
     return out
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m1: torch.Tensor, m2: torch.Tensor, step: int,
+              lr: float = 2e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              weight_decay: float = 0.0) -> None:
+    """rt_adam_step in place on float32 device tensors of equal size."""
+    _check("rt_adam_step", LIB.rt_adam_step(_ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), param.numel(), lr, beta1,
+                                            beta2, eps, weight_decay, step, _stream()))
 
 
 def gbuffer(gb: Dict[str, torch.Tensor]) -> RtGbuffer:
@@ -290,6 +302,19 @@ class Renderer:
             staging[k].copy_(gb_host[k], non_blocking=True)
         self.render_frame(staging, pixel_offset, out=out_dev)
         out_host.copy_(out_dev, non_blocking=True)
+
+    def distill_dirs(self, P: int, K: int, ray_offset: int = 0) -> torch.Tensor:
+        dirs = torch.empty(P, K, 4, device="cuda", dtype=torch.float32)
+        _check("rt_distill_dirs", LIB.rt_distill_dirs(self.ctx, P, K, ray_offset, _ptr(dirs), _stream()))
+        return dirs
+
+    def distill_backward(self, pos: torch.Tensor, normal: torch.Tensor, dirs: torch.Tensor, brdf_t: torch.Tensor,
+                         vis_t: torch.Tensor, depth_t: torch.Tensor, loss: Optional[torch.Tensor],
+                         g_table: torch.Tensor, g_brdf: torch.Tensor, g_irt: torch.Tensor) -> None:
+        P, K = dirs.shape[0], dirs.shape[1]
+        _check("rt_distill_backward", LIB.rt_distill_backward(
+            self.ctx, _ptr(pos), _ptr(normal), P, K, _ptr(dirs), _ptr(brdf_t), _ptr(vis_t), _ptr(depth_t),
+            _ptr(loss), _ptr(g_table), _ptr(g_brdf), _ptr(g_irt), _stream()))
 
     def backward(self, gb: Dict[str, torch.Tensor], d_radiance: torch.Tensor, g_table: torch.Tensor,
                  g_brdf: torch.Tensor, g_irt: torch.Tensor, pixel_offset: int = 0) -> None:

@@ -514,3 +514,54 @@ rt_status rt_denoise(int32_t width, int32_t height, const float* radiance, const
                                     reinterpret_cast<float4*>(work), reinterpret_cast<float4*>(out),
                                     (cudaStream_t)stream));
 }
+
+rt_status rt_distill_dirs(rt_ctx* ctx, int64_t P, int32_t K, int64_t ray_offset, float* dirs, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  int32_t S = 1;
+  while ((S + 1) * (S + 1) <= K) ++S;
+  if (P < 0 || K < 1 || K > 65536 || S * S != K || P * (int64_t)K > kMaxP || ray_offset < 0)
+    return RT_ERR_INVALID_ARG;
+  if (P == 0) return RT_OK;
+  if (!check_plane(dirs)) return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_distill_dirs((int)P, K, ray_offset, ctx->cfg.dir_seed, reinterpret_cast<float4*>(dirs),
+                                         (cudaStream_t)stream));
+}
+
+rt_status rt_distill_backward(rt_ctx* ctx, const float* pos, const float* normal, int64_t P, int32_t K,
+                              const float* dirs, const float* brdf_t, const float* vis_t, const float* depth_t,
+                              float* loss, float* g_table, float* g_brdf, float* g_irt, void* stream) {
+  rt_status st = check_ctx(ctx);
+  if (st != RT_OK) return st;
+  if (P < 0 || K < 1 || K > 65536 || P * (int64_t)K > kMaxP) return RT_ERR_INVALID_ARG;
+  if (ctx->cfg.precision != RT_FP32) return RT_ERR_UNSUPPORTED;
+  if (P == 0) return RT_OK;
+  if (!check_plane(pos) || !check_plane(normal) || !check_plane(dirs) || brdf_t == nullptr || !aligned(brdf_t, 4) ||
+      vis_t == nullptr || !aligned(vis_t, 4) || depth_t == nullptr || !aligned(depth_t, 4) ||
+      (loss != nullptr && !aligned(loss, 4)) || g_table == nullptr || !aligned(g_table, 8) || g_brdf == nullptr ||
+      !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))
+    return RT_ERR_INVALID_ARG;
+  return cuda_status(launch_distill_fp32(model_desc(ctx), reinterpret_cast<const float4*>(pos),
+                                         reinterpret_cast<const float4*>(normal), (int)P, K,
+                                         reinterpret_cast<const float4*>(dirs), brdf_t, vis_t, depth_t, loss, g_table,
+                                         g_brdf, g_irt, ctx->num_sms, (cudaStream_t)stream));
+}
+
+rt_status rt_adam_step(float* param, const float* grad, float* m1, float* m2, int64_t n, float lr, float beta1,
+                       float beta2, float eps, float weight_decay, int32_t step, void* stream) {
+  if (n < 0 || step < 1 || !std::isfinite(lr) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || !std::isfinite(weight_decay))
+    return RT_ERR_INVALID_ARG;
+  if (n == 0) return RT_OK;
+  if (param == nullptr || grad == nullptr || m1 == nullptr || m2 == nullptr || !aligned(param, 4) ||
+      !aligned(grad, 4) || !aligned(m1, 4) || !aligned(m2, 4))
+    return RT_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RT_ERR_CUDA;
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+  return cuda_status(launch_adam(param, grad, m1, m2, n, lr, beta1, beta2, eps, weight_decay, bc1, bc2, sms,
+                                 (cudaStream_t)stream));
+}

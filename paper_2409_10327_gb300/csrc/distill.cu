@@ -1,0 +1,337 @@
+// Per-head distillation of the hash renderer (Sec. 3.3 "Training Procedure";
+// supplementary "Training Details"): the stratified whole-sphere directions
+// (rt_distill_dirs), the FP32 adjoint of the per-head loss
+// (rt_distill_backward) and the Adam update (rt_adam_step).
+//
+// Loss, for P points x with normals n and K directions each:
+//   L1 over B's (n', a', r') against the teacher's, averaged over points and
+//   the 7 components; BCE of sigmoid(z0) against the teacher's visibility
+//   binarised at 0.5 and L1 of min(softplus(z1), 1) against the teacher's
+//   normalised depth, each averaged over the point's front-facing directions
+//   (w . n > 0) and then over points.
+//
+// Work unit: a warp takes 32 points.  For each of them it encodes f = H(x),
+// counts the front-facing directions and walks the directions 32 at a time
+// (lane = direction): I forward, the head gradients, I's adjoint with the
+// layer-1 f part shared by the rows, then scatters dLoss/df of the I part
+// into the table.  Then the warp runs B on its 32 points as one 32-row tile
+// (lane = point), back-propagates the L1 of the BRDF heads and scatters the
+// B part of dLoss/df.  Weight gradients go to the CTA's shared accumulator
+// (adjoint.cuh) and then to the caller's blobs.
+#include "adjoint.cuh"
+
+namespace rtk {
+
+namespace {
+
+constexpr int kDW = 3;                      // warps per CTA (shared memory holds one CTA of 3 warps)
+constexpr int kDT = 32 * kDW;
+// per-warp buffers (floats)
+constexpr int DB_F = 0;                                    // f of the warp's 32 points [32 cols]
+constexpr int DB_PE = DB_F + kActStride32;                 // PE of the current directions [32 cols]
+constexpr int DB_H1 = DB_PE + kActStride32;                // layer-1 activations [64 cols]
+constexpr int DB_H2 = DB_H1 + kActStride;                  // layer-2 activations, then dZ1 [64 cols]
+constexpr int DB_DZ2 = DB_H2 + kActStride;                 // dZ2 [64 cols]
+constexpr int DB_DZ = DB_DZ2 + kActStride;                 // output gradients [8][32]
+constexpr int DB_FP = DB_DZ + 8 * 32;                      // f of the current point [32]
+constexpr int DB_AP = DB_FP + 32;                          // b1 + W1f f of the current point [64]
+constexpr int DB_DFP = DB_AP + 64;                         // dLoss/df of the current point, I part [32]
+constexpr int DB_FLOATS = DB_DFP + 32;
+constexpr size_t kDSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kDW * DB_FLOATS) * sizeof(float);
+static_assert(DB_PE % 4 == 0 && DB_H1 % 4 == 0 && DB_H2 % 4 == 0 && DB_DZ2 % 4 == 0 && DB_DZ % 4 == 0 &&
+                  DB_FLOATS % 4 == 0,
+              "float4 alignment");
+
+__device__ __forceinline__ float sgnf(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
+
+__global__ void distill_dirs_kernel(long long PK, int K, int S, long long ray_offset, uint64_t seed,
+                                    float4* __restrict__ dirs) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= PK) return;
+  const long long p = e / K;
+  const int k = (int)(e - p * K);
+  const uint64_t ctr = (uint64_t)(ray_offset + p) * (uint64_t)K + (uint64_t)k;
+  const float xi1 = uniform24(splitmix64(seed, 2 * ctr + 1));
+  const float xi2 = uniform24(splitmix64(seed, 2 * ctr + 2));
+  const float u1 = ((float)(k / S) + xi1) / (float)S;
+  const float u2 = ((float)(k % S) + xi2) / (float)S;
+  const float z = 1.0f - 2.0f * u1;
+  const float rho = 2.0f * sqrtf(fmaxf(u1 * (1.0f - u1), 0.0f));
+  float sp, cp;
+  sincospif(2.0f * u2, &sp, &cp);
+  dirs[e] = make_float4(rho * cp, rho * sp, z, 0.0f);
+}
+
+__global__ void __launch_bounds__(kDT, 1)
+distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* __restrict__ nrm4, int P, int K,
+                    const float4* __restrict__ dirs, const float* __restrict__ brdf_t, const float* __restrict__ vis_t,
+                    const float* __restrict__ depth_t, float* __restrict__ loss, float* __restrict__ g_table,
+                    float* __restrict__ g_brdf, float* __restrict__ g_irt) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  float* sg = sw + WPACK_FLOATS;
+  for (int i = threadIdx.x; i < WPACK_FLOATS / 4; i += kDT)
+    smem4[i] = __ldg(reinterpret_cast<const float4*>(m.wpack) + i);
+  for (int i = threadIdx.x; i < G_FLOATS; i += kDT) sg[i] = 0.0f;
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 3, cg = lane & 7;
+  float* wb = sg + G_FLOATS + warp * DB_FLOATS;
+  float* F = wb + DB_F;
+  float* PEb = wb + DB_PE;
+  float* H1 = wb + DB_H1;
+  float* H2 = wb + DB_H2;
+  float* DZ2 = wb + DB_DZ2;
+  float* DZ = wb + DB_DZ;
+  float* fP = wb + DB_FP;
+  float* aP = wb + DB_AP;
+  float* dfP = wb + DB_DFP;
+  const int lf = m.lf, lfp = m.lfp, levels = m.grid.levels;
+  const float invR = 1.0f / (float)P;
+  const float inv_range = 1.0f / (m.far_t - m.near_t);
+  float l_brdf = 0.0f, l_bce = 0.0f, l_depth = 0.0f;
+
+  for (int g0 = (blockIdx.x * kDW + warp) * 32; g0 < P; g0 += gridDim.x * kDW * 32) {
+    // ---- I phase, one point at a time (lane = direction)
+    for (int pr = 0; pr < 32 && g0 + pr < P; ++pr) {
+      const int p = g0 + pr;
+      const f3 x = xyz(pos4[p]);
+      const f3 n = xyz(nrm4[p]);
+      {
+        const int l = lane >> 1;
+        float2 part = make_float2(0.f, 0.f);
+        if (l < levels) {
+          const float2 f = encode_level(m.grid, l, x);
+          part = (lane & 1) ? make_float2(0.f, 0.f) : f;
+        }
+        if ((lane & 1) == 0) {
+          fP[lane] = part.x;
+          fP[lane + 1] = part.y;
+        }
+        dfP[lane] = 0.0f;
+      }
+      __syncwarp();
+      F[aidx(lane, pr)] = fP[lane];   // f of point pr for the B phase (zero beyond L*F)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        float acc = sw[OFF_IB1 + c];
+        for (int k = 0; k < lfp; ++k) acc = fmaf(fP[k], sw[OFF_IW1F + k * 64 + c], acc);
+        aP[c] = acc;
+      }
+      int cnt = 0;
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        const bool ff = k < K && dot(xyz(dirs[(size_t)p * K + k]), n) > 0.0f;
+        cnt += __popc(__ballot_sync(0xffffffffu, ff));
+      }
+      const float wI = cnt > 0 ? invR / (float)cnt : 0.0f;
+      __syncwarp();
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < K;
+        const f3 w = valid ? xyz(dirs[(size_t)p * K + k]) : n;
+        const bool ff = valid && dot(w, n) > 0.0f;
+        float acc[8][8];
+        store_pe(PEb, w, lane);
+        __syncwarp();
+        zero(acc);
+        warp_gemm<kPEPad>(PEb, sw + OFF_IW1P, acc, rg, cg);
+        store_relu_colbias(H1, acc, aP, rg, cg);
+        __syncwarp();
+        zero(acc);
+        warp_gemm<kHidden>(H1, sw + OFF_IW2, acc, rg, cg);
+        store_relu_colbias(H2, acc, sw + OFF_IB2, rg, cg);
+        __syncwarp();
+        const float2 z = irt_head(H2, sw, lane);
+        float dz0 = 0.0f, dz1 = 0.0f;
+        if (ff) {
+          const size_t e = (size_t)p * K + k;
+          const float vt = vis_t[e] > 0.5f ? 1.0f : 0.0f;
+          const float dt = (depth_t[e] - m.near_t) * inv_range;
+          l_bce += wI * (fmaxf(z.x, 0.0f) - z.x * vt + log1pf(expf(-fabsf(z.x))));
+          dz0 = wI * (sigmoidf_(z.x) - vt);
+          const float sp = softplusf_(z.y);
+          const float d = fminf(sp, 1.0f) - dt;
+          l_depth += wI * fabsf(d);
+          dz1 = sp < 1.0f ? wI * sgnf(d) * sigmoidf_(z.y) : 0.0f;
+        }
+        DZ[lane] = dz0;
+        DZ[32 + lane] = dz1;
+        __syncwarp();
+        bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
+        bwd_w3<2>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
+        __syncwarp();
+        bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+        bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);          // dZ1 into H2
+        __syncwarp();
+        bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
+        // the f part of layer 1 is shared by the rows: dW1f[c][k] += f[k] colsum(dZ1)[c],
+        // dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = lane + 32 * h;
+          float cs = 0.0f;
+          for (int r = 0; r < 32; ++r) cs += H2[aidx(c, r)];
+          DZ2[c] = cs;
+        }
+        __syncwarp();
+        for (int kk = 0; kk < lf; ++kk) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            atomicAdd(sg + GI_W1 + c * LD_I1 + kk, fP[kk] * DZ2[c]);
+          }
+        }
+        if (lane < lf) {
+          float s = 0.0f;
+          for (int c = 0; c < 64; ++c) s = fmaf(DZ2[c], sw[OFF_IW1F + lane * 64 + c], s);
+          dfP[lane] += s;
+        }
+        __syncwarp();
+      }
+      {
+        const int l = lane >> 1;
+        if ((lane & 1) == 0 && l < levels)
+          encode_level_bwd(m.grid, l, x, dfP[lane], dfP[lane + 1], g_table, nullptr);
+      }
+      __syncwarp();
+    }
+
+    // ---- B phase: the warp's points as one 32-row tile (lane = point)
+    const int p = g0 + lane;
+    const bool vp = p < P;
+    if (!vp)
+      for (int k = 0; k < 32; ++k) F[aidx(k, lane)] = 0.0f;
+    __syncwarp();
+    float acc[8][8];
+    zero(acc);
+    warp_gemm_k(F, sw + OFF_BW1, acc, lfp, rg, cg);
+    store_relu_colbias(H1, acc, sw + OFF_BB1, rg, cg);
+    __syncwarp();
+    zero(acc);
+    warp_gemm<kHidden>(H1, sw + OFF_BW2, acc, rg, cg);
+    store_relu_colbias(H2, acc, sw + OFF_BB2, rg, cg);
+    __syncwarp();
+    float y[7];
+#pragma unroll
+    for (int o = 0; o < 7; ++o) y[o] = sw[OFF_BB3 + o];
+    for (int k = 0; k < kHidden; ++k) {
+      const float hk = H2[aidx(k, lane)];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) y[o] = fmaf(hk, sw[OFF_BW3 + 8 * k + o], y[o]);
+    }
+    const float nlen = sqrtf(fmaxf(y[0] * y[0] + y[1] * y[1] + y[2] * y[2], 1e-24f));
+    const f3 n2 = mk(y[0] / nlen, y[1] / nlen, y[2] / nlen);
+    const f3 a2 = mk(sigmoidf_(y[3]), sigmoidf_(y[4]), sigmoidf_(y[5]));
+    const float s6 = sigmoidf_(y[6]);
+    const float r2 = 0.09f + 0.91f * s6;
+    float dy[7];
+    {
+      const float wB = vp ? invR / 7.0f : 0.0f;
+      float t[7];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) t[o] = vp ? brdf_t[(size_t)p * 8 + o] : 0.0f;
+      const float out[7] = {n2.x, n2.y, n2.z, a2.x, a2.y, a2.z, r2};
+      float g[7];
+#pragma unroll
+      for (int o = 0; o < 7; ++o) {
+        l_brdf += wB * fabsf(out[o] - t[o]);
+        g[o] = wB * sgnf(out[o] - t[o]);
+      }
+      const f3 dn = mk(g[0], g[1], g[2]);
+      const float dnn = dot(n2, dn);
+      dy[0] = (dn.x - n2.x * dnn) / nlen;
+      dy[1] = (dn.y - n2.y * dnn) / nlen;
+      dy[2] = (dn.z - n2.z * dnn) / nlen;
+      dy[3] = g[3] * a2.x * (1.0f - a2.x);
+      dy[4] = g[4] * a2.y * (1.0f - a2.y);
+      dy[5] = g[5] * a2.z * (1.0f - a2.z);
+      dy[6] = g[6] * 0.91f * s6 * (1.0f - s6);
+    }
+#pragma unroll
+    for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
+    __syncwarp();
+    bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, DZ2, lane);
+    bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
+    __syncwarp();
+    bwd_weights(H1, 64, DZ2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+    bwd_hidden(DZ2, sw + OFF_BW2, H1, H2, lane);
+    __syncwarp();
+    bwd_weights(F, lf, H2, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+    float dF[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) dF[k] = 0.0f;
+    bwd_input(H2, sw + OFF_BW1, lf, dF, lane);
+    if (vp) {
+      const f3 x = xyz(pos4[p]);
+#pragma unroll
+      for (int l = 0; l < kMaxLevels; ++l)
+        if (l < levels) encode_level_bwd(m.grid, l, x, dF[2 * l], dF[2 * l + 1], g_table, nullptr);
+    }
+    __syncwarp();
+  }
+
+  // ---- loss terms (one atomic per warp) and the weight gradients
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l_brdf += __shfl_xor_sync(0xffffffffu, l_brdf, o);
+    l_bce += __shfl_xor_sync(0xffffffffu, l_bce, o);
+    l_depth += __shfl_xor_sync(0xffffffffu, l_depth, o);
+  }
+  if (lane == 0 && loss != nullptr) {
+    atomicAdd(loss + 0, l_brdf);
+    atomicAdd(loss + 1, l_bce);
+    atomicAdd(loss + 2, l_depth);
+  }
+  __syncthreads();
+  flush_weight_grads(sg, m.lf, g_brdf, g_irt, kDT);
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, long long n, float lr, float b1, float b2, float eps, float wd,
+                            float bc1, float bc2) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float gg = g[e] + wd * p[e];
+    const float a = b1 * m1[e] + (1.0f - b1) * gg;
+    const float b = b2 * m2[e] + (1.0f - b2) * gg * gg;
+    m1[e] = a;
+    m2[e] = b;
+    p[e] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+  }
+}
+
+}  // namespace
+
+cudaError_t prepare_distill() {
+  return cudaFuncSetAttribute(distill_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDSmem);
+}
+
+cudaError_t launch_distill_dirs(int P, int K, long long ray_offset, uint64_t seed, float4* dirs, cudaStream_t s) {
+  int S = 1;
+  while ((S + 1) * (S + 1) <= K) ++S;
+  const long long PK = (long long)P * K;
+  distill_dirs_kernel<<<(unsigned)((PK + 255) / 256), 256, 0, s>>>(PK, K, S, ray_offset, seed, dirs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distill_fp32(const ModelDesc& m, const float4* pos, const float4* nrm, int P, int K,
+                                const float4* dirs, const float* brdf_t, const float* vis_t, const float* depth_t,
+                                float* loss, float* g_table, float* g_brdf, float* g_irt, int num_sms, cudaStream_t s) {
+  const int need = (P + 32 * kDW - 1) / (32 * kDW);
+  const int grid = need < num_sms ? need : num_sms;
+  distill_fp32_kernel<<<grid, kDT, kDSmem, s>>>(m, pos, nrm, P, K, dirs, brdf_t, vis_t, depth_t, loss, g_table,
+                                                g_brdf, g_irt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, long long n, float lr, float b1, float b2,
+                        float eps, float wd, float bc1, float bc2, int num_sms, cudaStream_t s) {
+  const long long blocks = (n + 255) / 256;
+  const int grid = (int)(blocks < 8LL * num_sms ? blocks : 8LL * num_sms);
+  adam_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(p, g, m1, m2, n, lr, b1, b2, eps, wd, bc1, bc2);
+  return cudaGetLastError();
+}
+
+}  // namespace rtk

@@ -130,6 +130,13 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
 constexpr uint32_t kStatusTimeout = 1u << 28;
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                float4* out, int num_sms, cudaStream_t s);
+cudaError_t prepare_distill();
+cudaError_t launch_distill_dirs(int P, int K, long long ray_offset, uint64_t seed, float4* dirs, cudaStream_t s);
+cudaError_t launch_distill_fp32(const ModelDesc& m, const float4* pos, const float4* nrm, int P, int K,
+                                const float4* dirs, const float* brdf_t, const float* vis_t, const float* depth_t,
+                                float* loss, float* g_table, float* g_brdf, float* g_irt, int num_sms, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, long long n, float lr, float b1, float b2,
+                        float eps, float wd, float bc1, float bc2, int num_sms, cudaStream_t s);
 cudaError_t launch_env_cdf(const float4* env, int H, int W, float* cdf_m, float* cdf_c, cudaStream_t s);
 cudaError_t launch_denoise(int W, int H, const float4* rad, const float* z, const float4* nrm, int iterations,
                            float sigma_z, float sigma_n, float sigma_l, float4* work, float4* out, cudaStream_t s);

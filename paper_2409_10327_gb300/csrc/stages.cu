@@ -250,6 +250,7 @@ cudaError_t prepare_kernels() {
   cudaError_t e = prepare_render_fp32();
   if (e == cudaSuccess) e = prepare_render_bf16();
   if (e == cudaSuccess) e = prepare_backward_fp32();
+  if (e == cudaSuccess) e = prepare_distill();
   return e;
 }
 
