@@ -379,12 +379,7 @@ def run_ours(args, cfg):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world > 1:
-            tt = torch.tensor([x], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            return float(tt.item())
-        return x
+    from paper_2409_10327_gb300.parallel import max_over_ranks
 
     renderers, gbs = _setup(cfg, rank)
     out = torch.empty(cfg.n_pixels, 4, device="cuda")
