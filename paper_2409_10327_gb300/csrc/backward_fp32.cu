@@ -27,22 +27,22 @@ namespace rtk {
 
 namespace {
 
-constexpr int kBW = 3;                     // warps per CTA
+constexpr int kBW = 4;                     // warps per CTA
 constexpr int kBT = 32 * kBW;
 // per-warp buffers (floats)
 constexpr int WB_F2 = 0;                                   // f' of the chunk's rows  [32 cols]
 constexpr int WB_PE = WB_F2 + kActStride32;                 // PE of the current direction [32 cols]
 constexpr int WB_H1 = WB_PE + kActStride32;                 // layer-1 activations [64 cols]
-constexpr int WB_H2 = WB_H1 + kActStride;                   // layer-2 activations, then dZ1 [64 cols]
-constexpr int WB_DZ2 = WB_H2 + kActStride;                  // dZ2 [64 cols]
-constexpr int WB_DZ = WB_DZ2 + kActStride;                  // output gradients [8][32]
+constexpr int WB_H2 = WB_H1 + kActStride;                   // layer-2 activations, then dZ2 (in place) [64 cols]
+constexpr int WB_DZ = WB_H2 + kActStride;                  // output gradients [8][32]
 constexpr int WB_FP = WB_DZ + 8 * 32;                       // primary feature f [32]
 constexpr int WB_AP = WB_FP + 32;                           // primary b1 + W1f f [64]
 constexpr int WB_DFP = WB_AP + 64;                          // dLoss/df of the pixel [32]
 constexpr int WB_FLOATS = WB_DFP + 32;
 constexpr size_t kBSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kBW * WB_FLOATS) * sizeof(float);
 static_assert(LD_I1 >= 32 + 27 + 1 && LD_B1 >= 33, "gradient rows");
-static_assert(WB_F2 % 4 == 0 && WB_PE % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 && WB_DZ2 % 4 == 0 &&
+static_assert(kBSmem <= 232448, "one CTA per SM");
+static_assert(WB_F2 % 4 == 0 && WB_PE % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 &&
                   WB_DZ % 4 == 0 && WB_FLOATS % 4 == 0 && G_FLOATS % 4 == 0,
               "float4 alignment");
 
@@ -113,7 +113,6 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
   float* PEb = wb + WB_PE;
   float* H1 = wb + WB_H1;
   float* H2 = wb + WB_H2;
-  float* DZ2 = wb + WB_DZ2;
   float* DZ = wb + WB_DZ;
   float* fP = wb + WB_FP;
   float* aP = wb + WB_AP;
@@ -261,15 +260,17 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
         DZ[lane] = dz0;
         __syncwarp();
         // I backward: head, W3, W2, hidden, W1 (f' and PE parts), input f'
-        bwd_head<1, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
         bwd_w3<1>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
         __syncwarp();
-        bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
-        bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);          // dZ1 into H2
+        bwd_head<1, 2>(H2, DZ, sw + OFF_IW3, H2, lane);   // dZ2 over H2, in place
         __syncwarp();
-        bwd_weights(F2, lf, H2, sg + GI_W1, LD_I1, 0, sg + GI_B1, lane);
-        bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, nullptr, lane);
-        bwd_input(H2, sw + OFF_IW1F, lf, dF2, lane);
+        bwd_weights(H1, 64, H2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+        __syncwarp();
+        bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
+        __syncwarp();
+        bwd_weights(F2, lf, H1, sg + GI_W1, LD_I1, 0, sg + GI_B1, lane);
+        bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, nullptr, lane);
+        bwd_input(H1, sw + OFF_IW1F, lf, dF2, lane);
       }
       lo2 = lo2 * sM;
       const float dv = dot(dli, e1 - lo2);
@@ -297,14 +298,16 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
 #pragma unroll
       for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
       __syncwarp();
-      bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, DZ2, lane);
       bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
       __syncwarp();
-      bwd_weights(H1, 64, DZ2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
-      bwd_hidden(DZ2, sw + OFF_BW2, H1, H2, lane);
+      bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, H2, lane);   // dZ2 over H2, in place
       __syncwarp();
-      bwd_weights(F2, lf, H2, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
-      bwd_input(H2, sw + OFF_BW1, lf, dF2, lane);
+      bwd_weights(H1, 64, H2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+      __syncwarp();
+      bwd_hidden(H2, sw + OFF_BW2, H1, H1, lane);   // dZ1 over H1, in place
+      __syncwarp();
+      bwd_weights(F2, lf, H1, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+      bwd_input(H1, sw + OFF_BW1, lf, dF2, lane);
 
       // ---- encode adjoint at x': table gradients and dLoss/dx'
       f3 dx2 = mk(0.f, 0.f, 0.f);
@@ -338,33 +341,35 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       DZ[lane] = dz0p;
       DZ[32 + lane] = valid ? dz1 : 0.0f;
       __syncwarp();
-      bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
       bwd_w3<2>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
       __syncwarp();
-      bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
-      bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);
+      bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, H2, lane);   // dZ2 over H2, in place
       __syncwarp();
-      bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
+      bwd_weights(H1, 64, H2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+      __syncwarp();
+      bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
+      __syncwarp();
+      bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
       // the f part of layer 1 is shared by the chunk's rows: dW1f[c][k] += f[k] colsum(dZ1)[c]
       // and dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = lane + 32 * h;
         float cs = 0.0f;
-        for (int r = 0; r < 32; ++r) cs += H2[aidx(c, r)];
-        DZ2[c] = cs;   // reuse as scratch: column sums of dZ1
+        for (int r = 0; r < 32; ++r) cs += H1[aidx(c, r)];
+        H2[c] = cs;   // scratch: column sums of dZ1 (dZ2 is no longer needed)
       }
       __syncwarp();
       for (int k = 0; k < lf; ++k) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = lane + 32 * h;
-          atomicAdd(sg + GI_W1 + c * LD_I1 + k, fP[k] * DZ2[c]);
+          atomicAdd(sg + GI_W1 + c * LD_I1 + k, fP[k] * H2[c]);
         }
       }
       if (lane < lf) {
         float s = 0.0f;
-        for (int c = 0; c < 64; ++c) s = fmaf(DZ2[c], sw[OFF_IW1F + lane * 64 + c], s);
+        for (int c = 0; c < 64; ++c) s = fmaf(H2[c], sw[OFF_IW1F + lane * 64 + c], s);
         dfP[lane] += s;
       }
       __syncwarp();

@@ -24,21 +24,21 @@ namespace rtk {
 
 namespace {
 
-constexpr int kDW = 3;                      // warps per CTA (shared memory holds one CTA of 3 warps)
+constexpr int kDW = 4;                      // warps per CTA (shared memory holds one CTA of 4 warps)
 constexpr int kDT = 32 * kDW;
 // per-warp buffers (floats)
 constexpr int DB_F = 0;                                    // f of the warp's 32 points [32 cols]
 constexpr int DB_PE = DB_F + kActStride32;                 // PE of the current directions [32 cols]
 constexpr int DB_H1 = DB_PE + kActStride32;                // layer-1 activations [64 cols]
-constexpr int DB_H2 = DB_H1 + kActStride;                  // layer-2 activations, then dZ1 [64 cols]
-constexpr int DB_DZ2 = DB_H2 + kActStride;                 // dZ2 [64 cols]
-constexpr int DB_DZ = DB_DZ2 + kActStride;                 // output gradients [8][32]
+constexpr int DB_H2 = DB_H1 + kActStride;                  // layer-2 activations, then dZ2 (in place) [64 cols]
+constexpr int DB_DZ = DB_H2 + kActStride;                 // output gradients [8][32]
 constexpr int DB_FP = DB_DZ + 8 * 32;                      // f of the current point [32]
 constexpr int DB_AP = DB_FP + 32;                          // b1 + W1f f of the current point [64]
 constexpr int DB_DFP = DB_AP + 64;                         // dLoss/df of the current point, I part [32]
 constexpr int DB_FLOATS = DB_DFP + 32;
 constexpr size_t kDSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kDW * DB_FLOATS) * sizeof(float);
-static_assert(DB_PE % 4 == 0 && DB_H1 % 4 == 0 && DB_H2 % 4 == 0 && DB_DZ2 % 4 == 0 && DB_DZ % 4 == 0 &&
+static_assert(kDSmem <= 232448, "one CTA per SM");
+static_assert(DB_PE % 4 == 0 && DB_H1 % 4 == 0 && DB_H2 % 4 == 0 && DB_DZ % 4 == 0 &&
                   DB_FLOATS % 4 == 0,
               "float4 alignment");
 
@@ -82,7 +82,6 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
   float* PEb = wb + DB_PE;
   float* H1 = wb + DB_H1;
   float* H2 = wb + DB_H2;
-  float* DZ2 = wb + DB_DZ2;
   float* DZ = wb + DB_DZ;
   float* fP = wb + DB_FP;
   float* aP = wb + DB_AP;
@@ -160,33 +159,35 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
         DZ[lane] = dz0;
         DZ[32 + lane] = dz1;
         __syncwarp();
-        bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, DZ2, lane);
         bwd_w3<2>(H2, DZ, sg + GI_W3, sg + GI_B3, lane);
         __syncwarp();
-        bwd_weights(H1, 64, DZ2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
-        bwd_hidden(DZ2, sw + OFF_IW2, H1, H2, lane);          // dZ1 into H2
+        bwd_head<2, 2>(H2, DZ, sw + OFF_IW3, H2, lane);   // dZ2 over H2, in place
         __syncwarp();
-        bwd_weights(PEb, kPE, H2, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
+        bwd_weights(H1, 64, H2, sg + GI_W2, LD_2, 0, sg + GI_B2, lane);
+        __syncwarp();
+        bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
+        __syncwarp();
+        bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
         // the f part of layer 1 is shared by the rows: dW1f[c][k] += f[k] colsum(dZ1)[c],
         // dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = lane + 32 * h;
           float cs = 0.0f;
-          for (int r = 0; r < 32; ++r) cs += H2[aidx(c, r)];
-          DZ2[c] = cs;
+          for (int r = 0; r < 32; ++r) cs += H1[aidx(c, r)];
+          H2[c] = cs;   // scratch: column sums of dZ1 (dZ2 is no longer needed)
         }
         __syncwarp();
         for (int kk = 0; kk < lf; ++kk) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
-            atomicAdd(sg + GI_W1 + c * LD_I1 + kk, fP[kk] * DZ2[c]);
+            atomicAdd(sg + GI_W1 + c * LD_I1 + kk, fP[kk] * H2[c]);
           }
         }
         if (lane < lf) {
           float s = 0.0f;
-          for (int c = 0; c < 64; ++c) s = fmaf(DZ2[c], sw[OFF_IW1F + lane * 64 + c], s);
+          for (int c = 0; c < 64; ++c) s = fmaf(H2[c], sw[OFF_IW1F + lane * 64 + c], s);
           dfP[lane] += s;
         }
         __syncwarp();
@@ -253,17 +254,19 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
 #pragma unroll
     for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
     __syncwarp();
-    bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, DZ2, lane);
     bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
     __syncwarp();
-    bwd_weights(H1, 64, DZ2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
-    bwd_hidden(DZ2, sw + OFF_BW2, H1, H2, lane);
+    bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, H2, lane);   // dZ2 over H2, in place
     __syncwarp();
-    bwd_weights(F, lf, H2, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+    bwd_weights(H1, 64, H2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+    __syncwarp();
+    bwd_hidden(H2, sw + OFF_BW2, H1, H1, lane);   // dZ1 over H1, in place
+    __syncwarp();
+    bwd_weights(F, lf, H1, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
     float dF[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) dF[k] = 0.0f;
-    bwd_input(H2, sw + OFF_BW1, lf, dF, lane);
+    bwd_input(H1, sw + OFF_BW1, lf, dF, lane);
     if (vp) {
       const f3 x = xyz(pos4[p]);
 #pragma unroll
