@@ -1,5 +1,7 @@
 // Shared pieces of the hand-written FP32 adjoints (rt_backward, rt_distill_backward):
-// the per-CTA weight-gradient accumulator in shared memory, the warp-level
+// the per-CTA weight-gradient accumulator of I in shared memory (I runs 1 + M
+// times per row chunk; B, which runs once, adds its gradients straight into
+// the caller's blob with global atomics: BlobB gives its offsets), the warp-level
 // adjoints of the MLP layers (one row per lane, activations in the k-major
 // layout of warp_gemm.cuh) and of the trilinear hash encode, and the flush
 // of the accumulator into the caller's gradient blobs.
@@ -9,15 +11,24 @@
 
 namespace rtk {
 
-// gradient accumulator layout in shared memory (floats; rows padded to K + 1)
+// I's gradient accumulator in shared memory (floats; rows padded to K + 1)
 constexpr int LD_I1 = 60;                  // >= L*F + 27 + 1
-constexpr int LD_B1 = 33;                  // >= L*F + 1
 constexpr int LD_2 = 65;
 constexpr int GI_W1 = 0, GI_B1 = GI_W1 + 64 * LD_I1, GI_W2 = GI_B1 + 64, GI_B2 = GI_W2 + 64 * LD_2;
 constexpr int GI_W3 = GI_B2 + 64, GI_B3 = GI_W3 + 2 * LD_2;
-constexpr int GB_W1 = GI_B3 + 4, GB_B1 = GB_W1 + 64 * LD_B1, GB_W2 = GB_B1 + 64, GB_B2 = GB_W2 + 64 * LD_2;
-constexpr int GB_W3 = GB_B2 + 64, GB_B3 = GB_W3 + 7 * LD_2;
-constexpr int G_FLOATS = (GB_B3 + 8 + 3) / 4 * 4;
+constexpr int G_FLOATS = (GI_B3 + 2 + 3) / 4 * 4;
+
+// B's gradient blob (canonical layout of rt_param_count: W1 [64][lf], b1, W2 [64][64], b2, W3 [7][64], b3)
+struct BlobB {
+  float* g;
+  int lf;
+  __device__ __forceinline__ float* w1() const { return g; }
+  __device__ __forceinline__ float* b1() const { return g + 64 * lf; }
+  __device__ __forceinline__ float* w2() const { return g + 64 * lf + 64; }
+  __device__ __forceinline__ float* b2() const { return g + 64 * lf + 64 + 4096; }
+  __device__ __forceinline__ float* w3() const { return g + 64 * lf + 128 + 4096; }
+  __device__ __forceinline__ float* b3() const { return g + 64 * lf + 128 + 4096 + 448; }
+};
 // DZ2(c, row) = (sum_o dz[o][row] W3[c][o]) * [H2(c, row) > 0]   (thread per row)
 template <int NOUT, int LDW>
 __device__ __forceinline__ void bwd_head(const float* H2, const float* dz, const float* W3, float* DZ2, int lane) {
@@ -35,8 +46,9 @@ __device__ __forceinline__ void bwd_head(const float* H2, const float* dz, const
 
 // dW3[o][k] += sum_rows H2(k, row) dz[o][row]; db3[o] += sum_rows dz[o][row]
 template <int NOUT>
-__device__ __forceinline__ void bwd_w3(const float* H2, const float* dz, float* gW3, float* gb3, int lane) {
-#pragma unroll
+__device__ __forceinline__ void bwd_w3(const float* H2, const float* dz, float* gW3, float* gb3, int lane,
+                                       int ld = LD_2) {
+#pragma unroll 1   // rolled: unrolled, the two passes' global atomics keep too many registers live
   for (int kk = 0; kk < 2; ++kk) {
     const int k = 2 * lane + kk;
     float acc[NOUT];
@@ -48,7 +60,7 @@ __device__ __forceinline__ void bwd_w3(const float* H2, const float* dz, float* 
       for (int o = 0; o < NOUT; ++o) acc[o] = fmaf(h, dz[o * 32 + r], acc[o]);
     }
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) atomicAdd(gW3 + o * LD_2 + k, acc[o]);
+    for (int o = 0; o < NOUT; ++o) atomicAdd(gW3 + o * ld + k, acc[o]);
   }
   if (lane < NOUT) {
     float s = 0.0f;
@@ -174,29 +186,19 @@ __device__ __forceinline__ void encode_level_bwd(const GridDesc& g, int l, f3 x,
   }
 }
 
-// Add the CTA's accumulated weight gradients into the caller's blobs
-// (canonical layouts of rt_param_count); called by all threads after a barrier.
-__device__ __forceinline__ void flush_weight_grads(const float* sg, int lf, float* __restrict__ g_brdf,
-                                                   float* __restrict__ g_irt, int nthreads) {
-  const int lfv = lf, in_i = lfv + kPE;
+// Add the CTA's accumulated gradients of I into the caller's blob (canonical
+// layout of rt_param_count); called by all threads after a barrier.
+__device__ __forceinline__ void flush_irt_grads(const float* sg, int lf, float* __restrict__ g_irt, int nthreads) {
+  const int in_i = lf + kPE;
   const int iW1 = 0, iB1 = 64 * in_i, iW2 = iB1 + 64, iB2 = iW2 + 4096, iW3 = iB2 + 64, iB3 = iW3 + 128;
-  const int bW1 = 0, bB1 = 64 * lfv, bW2 = bB1 + 64, bB2 = bW2 + 4096, bW3 = bB2 + 64, bB3 = bW3 + 448;
   for (int e = threadIdx.x; e < 64 * in_i; e += nthreads) atomicAdd(g_irt + iW1 + e, sg[GI_W1 + (e / in_i) * LD_I1 + e % in_i]);
   for (int e = threadIdx.x; e < 64; e += nthreads) {
     atomicAdd(g_irt + iB1 + e, sg[GI_B1 + e]);
     atomicAdd(g_irt + iB2 + e, sg[GI_B2 + e]);
-    atomicAdd(g_brdf + bB1 + e, sg[GB_B1 + e]);
-    atomicAdd(g_brdf + bB2 + e, sg[GB_B2 + e]);
   }
-  for (int e = threadIdx.x; e < 4096; e += nthreads) {
-    atomicAdd(g_irt + iW2 + e, sg[GI_W2 + (e / 64) * LD_2 + e % 64]);
-    atomicAdd(g_brdf + bW2 + e, sg[GB_W2 + (e / 64) * LD_2 + e % 64]);
-  }
+  for (int e = threadIdx.x; e < 4096; e += nthreads) atomicAdd(g_irt + iW2 + e, sg[GI_W2 + (e / 64) * LD_2 + e % 64]);
   for (int e = threadIdx.x; e < 128; e += nthreads) atomicAdd(g_irt + iW3 + e, sg[GI_W3 + (e / 64) * LD_2 + e % 64]);
   for (int e = threadIdx.x; e < 2; e += nthreads) atomicAdd(g_irt + iB3 + e, sg[GI_B3 + e]);
-  for (int e = threadIdx.x; e < 64 * lfv; e += nthreads) atomicAdd(g_brdf + bW1 + e, sg[GB_W1 + (e / lfv) * LD_B1 + e % lfv]);
-  for (int e = threadIdx.x; e < 448; e += nthreads) atomicAdd(g_brdf + bW3 + e, sg[GB_W3 + (e / 64) * LD_2 + e % 64]);
-  for (int e = threadIdx.x; e < 7; e += nthreads) atomicAdd(g_brdf + bB3 + e, sg[GB_B3 + e]);
 }
 
 }  // namespace rtk

@@ -27,7 +27,7 @@ namespace rtk {
 
 namespace {
 
-constexpr int kBW = 4;                     // warps per CTA
+constexpr int kBW = 5;                     // warps per CTA
 constexpr int kBT = 32 * kBW;
 // per-warp buffers (floats)
 constexpr int WB_F2 = 0;                                   // f' of the chunk's rows  [32 cols]
@@ -40,7 +40,7 @@ constexpr int WB_AP = WB_FP + 32;                           // primary b1 + W1f 
 constexpr int WB_DFP = WB_AP + 64;                          // dLoss/df of the pixel [32]
 constexpr int WB_FLOATS = WB_DFP + 32;
 constexpr size_t kBSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kBW * WB_FLOATS) * sizeof(float);
-static_assert(LD_I1 >= 32 + 27 + 1 && LD_B1 >= 33, "gradient rows");
+static_assert(LD_I1 >= 32 + 27 + 1, "gradient rows");
 static_assert(kBSmem <= 232448, "one CTA per SM");
 static_assert(WB_F2 % 4 == 0 && WB_PE % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 &&
                   WB_DZ % 4 == 0 && WB_FLOATS % 4 == 0 && G_FLOATS % 4 == 0,
@@ -119,6 +119,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
   float* dfP = wb + WB_DFP;
   const int N = m.N, M = m.M, lf = m.lf, lfp = m.lfp;
   const bool disney = !m.lambert;
+  const BlobB gB{g_brdf, lf};
   const float4* pos4 = reinterpret_cast<const float4*>(gb.pos);
   const float4* nrm4 = reinterpret_cast<const float4*>(gb.normal);
   const float4* view4 = reinterpret_cast<const float4*>(gb.view);
@@ -298,15 +299,15 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
 #pragma unroll
       for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
       __syncwarp();
-      bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
+      bwd_w3<7>(H2, DZ, gB.w3(), gB.b3(), lane, 64);
       __syncwarp();
       bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, H2, lane);   // dZ2 over H2, in place
       __syncwarp();
-      bwd_weights(H1, 64, H2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+      bwd_weights(H1, 64, H2, gB.w2(), 64, 0, gB.b2(), lane);
       __syncwarp();
       bwd_hidden(H2, sw + OFF_BW2, H1, H1, lane);   // dZ1 over H1, in place
       __syncwarp();
-      bwd_weights(F2, lf, H1, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+      bwd_weights(F2, lf, H1, gB.w1(), lf, 0, gB.b1(), lane);
       bwd_input(H1, sw + OFF_BW1, lf, dF2, lane);
 
       // ---- encode adjoint at x': table gradients and dLoss/dx'
@@ -385,7 +386,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
 
   // ---- flush the CTA's weight gradients into the caller's blobs (canonical layouts)
   __syncthreads();
-  flush_weight_grads(sg, m.lf, g_brdf, g_irt, kBT);
+  flush_irt_grads(sg, m.lf, g_irt, kBT);
 }
 
 }  // namespace

@@ -24,7 +24,7 @@ namespace rtk {
 
 namespace {
 
-constexpr int kDW = 4;                      // warps per CTA (shared memory holds one CTA of 4 warps)
+constexpr int kDW = 5;                      // warps per CTA (shared memory holds one CTA of 5 warps)
 constexpr int kDT = 32 * kDW;
 // per-warp buffers (floats)
 constexpr int DB_F = 0;                                    // f of the warp's 32 points [32 cols]
@@ -87,6 +87,7 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
   float* aP = wb + DB_AP;
   float* dfP = wb + DB_DFP;
   const int lf = m.lf, lfp = m.lfp, levels = m.grid.levels;
+  const BlobB gB{g_brdf, lf};
   const float invR = 1.0f / (float)P;
   const float inv_range = 1.0f / (m.far_t - m.near_t);
   float l_brdf = 0.0f, l_bce = 0.0f, l_depth = 0.0f;
@@ -254,15 +255,15 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
 #pragma unroll
     for (int o = 0; o < 7; ++o) DZ[o * 32 + lane] = dy[o];
     __syncwarp();
-    bwd_w3<7>(H2, DZ, sg + GB_W3, sg + GB_B3, lane);
+    bwd_w3<7>(H2, DZ, gB.w3(), gB.b3(), lane, 64);
     __syncwarp();
     bwd_head<7, 8>(H2, DZ, sw + OFF_BW3, H2, lane);   // dZ2 over H2, in place
     __syncwarp();
-    bwd_weights(H1, 64, H2, sg + GB_W2, LD_2, 0, sg + GB_B2, lane);
+    bwd_weights(H1, 64, H2, gB.w2(), 64, 0, gB.b2(), lane);
     __syncwarp();
     bwd_hidden(H2, sw + OFF_BW2, H1, H1, lane);   // dZ1 over H1, in place
     __syncwarp();
-    bwd_weights(F, lf, H1, sg + GB_W1, LD_B1, 0, sg + GB_B1, lane);
+    bwd_weights(F, lf, H1, gB.w1(), lf, 0, gB.b1(), lane);
     float dF[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) dF[k] = 0.0f;
@@ -289,7 +290,7 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
     atomicAdd(loss + 2, l_depth);
   }
   __syncthreads();
-  flush_weight_grads(sg, m.lf, g_brdf, g_irt, kDT);
+  flush_irt_grads(sg, m.lf, g_irt, kDT);
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
