@@ -18,7 +18,8 @@ struct rt_ctx {
   float* wpack;        // WPACK_FLOATS
   uint8_t* wbf16;      // WBF16_BYTES
   uint32_t* status;    // device status word
-  float* cdf;          // MIS texel CDFs: marginal [env_h + 1], then conditional [env_h][env_w + 1]
+  float* cdf;          // MIS texel CDFs: marginal [env_h + 1], then conditional [env_h][env_w + 1],
+                       // then the int cutpoint tables [2^gm_shift] and [env_h][2^gc_shift]
   const void* table;
   const float* env;
   HeadParams head;     // host copy of the FP32 output layers (BF16 kernel parameter)
@@ -46,6 +47,11 @@ bool level_dense(const rt_config* c, int res) {
 }
 
 int64_t cdf_floats(const rt_config& c) { return (int64_t)(c.env_h + 1) + (int64_t)c.env_h * (c.env_w + 1); }
+int64_t cdf_words(const rt_config& c) {
+  return cdf_floats(c) + (1LL << guide_shift(c.env_h)) + (int64_t)c.env_h * (1LL << guide_shift(c.env_w));
+}
+int* guide_m_of(float* cdf, const rt_config& c) { return reinterpret_cast<int*>(cdf + cdf_floats(c)); }
+int* guide_c_of(float* cdf, const rt_config& c) { return guide_m_of(cdf, c) + (1 << guide_shift(c.env_h)); }
 
 ModelDesc model_desc(const rt_ctx* ctx) {
   ModelDesc m{};
@@ -78,6 +84,10 @@ ModelDesc model_desc(const rt_ctx* ctx) {
   m.mis = c.sampling == RT_SAMPLE_MIS ? 1 : 0;
   m.cdf_m = ctx->cdf;
   m.cdf_c = ctx->cdf + (c.env_h + 1);
+  m.guide_m = guide_m_of(ctx->cdf, c);
+  m.guide_c = guide_c_of(ctx->cdf, c);
+  m.gm_shift = guide_shift(c.env_h);
+  m.gc_shift = guide_shift(c.env_w);
   m.lambert = c.brdf_mode == RT_LAMBERT;
   m.seed = c.dir_seed;
   return m;
@@ -182,7 +192,7 @@ int64_t rt_param_count(const rt_config* c, int32_t which) {
 
 int64_t rt_workspace_bytes(const rt_config* c) {
   if (rt_config_validate(c) != RT_OK) return -1;
-  return (int64_t)WPACK_FLOATS * 4 + WBF16_BYTES + 256 + cdf_floats(*c) * 4;
+  return (int64_t)WPACK_FLOATS * 4 + WBF16_BYTES + 256 + cdf_words(*c) * 4;
 }
 
 rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
@@ -219,7 +229,7 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
     delete ctx;
     return RT_ERR_OOM;
   }
-  if (cudaMalloc(&ctx->cdf, (size_t)cdf_floats(*cfg) * 4) != cudaSuccess) {
+  if (cudaMalloc(&ctx->cdf, (size_t)cdf_words(*cfg) * 4) != cudaSuccess) {
     cudaFree(ctx->wpack);
     cudaFree(ctx->wbf16);
     cudaFree(ctx->status);
@@ -264,7 +274,9 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
   rt_status st = cuda_status(launch_repack(brdf_w, irt_w, lf, ctx->wpack, s));
   if (st == RT_OK)
     st = cuda_status(launch_env_cdf(reinterpret_cast<const float4*>(env), ctx->cfg.env_h, ctx->cfg.env_w, ctx->cdf,
-                                    ctx->cdf + (ctx->cfg.env_h + 1), s));
+                                    ctx->cdf + (ctx->cfg.env_h + 1), guide_m_of(ctx->cdf, ctx->cfg),
+                                    guide_shift(ctx->cfg.env_h), guide_c_of(ctx->cdf, ctx->cfg),
+                                    guide_shift(ctx->cfg.env_w), s));
   if (st == RT_OK) st = cuda_status(launch_repack_bf16(ctx->wpack, ctx->wbf16, s));
   if (st != RT_OK) return st;
   // host copy of the output layers for the BF16 kernel's parameters

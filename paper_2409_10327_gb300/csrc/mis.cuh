@@ -30,13 +30,31 @@ __device__ __forceinline__ int cdf_find(const float* __restrict__ cdf, int n, fl
   return lo;
 }
 
+// cdf_find with a cutpoint table (Chen & Asau's guide table): guide[j] =
+// cdf_find(cdf, n, j / G) for G = 2^gshift.  For u in [j, j + 1) / G the
+// answer lies in [guide[j], guide[j + 1]] because the CDF does not decrease,
+// so the bisection over that range returns the same index as over [0, n).
+__device__ __forceinline__ int cdf_find_guided(const float* __restrict__ cdf, int n, float u,
+                                               const int* __restrict__ guide, int gshift) {
+  const int G = 1 << gshift;
+  const int j = min((int)(u * (float)G), G - 1);   // exact: G is a power of two
+  int lo = __ldg(guide + j);
+  int hi = j + 1 < G ? min(__ldg(guide + j + 1) + 1, n) : n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(cdf + mid) <= u) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ f3 mis_light_direction(const ModelDesc& m, float u1, float u2) {
   const int H = m.env_h, W = m.env_w;
-  const int r = cdf_find(m.cdf_m, H, u1);
+  const int r = cdf_find_guided(m.cdf_m, H, u1, m.guide_m, m.gm_shift);
   const float m0 = __ldg(m.cdf_m + r), m1 = __ldg(m.cdf_m + r + 1);
   const float ur = (u1 - m0) / (m1 - m0);
   const float* row = m.cdf_c + (size_t)r * (W + 1);
-  const int c = cdf_find(row, W, u2);
+  const int c = cdf_find_guided(row, W, u2, m.guide_c + ((size_t)r << m.gc_shift), m.gc_shift);
   const float c0 = __ldg(row + c), c1 = __ldg(row + c + 1);
   const float uc = (u2 - c0) / (c1 - c0);
   const float theta = kPi * ((float)r + ur) / (float)H;

@@ -89,6 +89,9 @@ struct ModelDesc {
   int mis;                     // 1: MIS primary directions (RT_SAMPLE_MIS)
   const float* cdf_m;          // [env_h + 1] marginal CDF of the bound map's texel distribution
   const float* cdf_c;          // [env_h][env_w + 1] conditional CDFs
+  const int* guide_m;          // [1 << gm_shift] cutpoints of cdf_m: the search's start for u in [j, j + 1) / 2^gm_shift
+  const int* guide_c;          // [env_h][1 << gc_shift] cutpoints of each conditional CDF
+  int gm_shift, gc_shift;
   int lambert;
   uint64_t seed;
 };
@@ -137,7 +140,14 @@ cudaError_t launch_distill_fp32(const ModelDesc& m, const float4* pos, const flo
                                 float* loss, float* g_table, float* g_brdf, float* g_irt, int num_sms, cudaStream_t s);
 cudaError_t launch_adam(float* p, const float* g, float* m1, float* m2, long long n, float lr, float b1, float b2,
                         float eps, float wd, float bc1, float bc2, int num_sms, cudaStream_t s);
-cudaError_t launch_env_cdf(const float4* env, int H, int W, float* cdf_m, float* cdf_c, cudaStream_t s);
+cudaError_t launch_env_cdf(const float4* env, int H, int W, float* cdf_m, float* cdf_c, int* guide_m, int gm_shift,
+                           int* guide_c, int gc_shift, cudaStream_t s);
+// smallest s with 2^s >= n (n >= 1): the cutpoint tables have 2^s entries
+inline int guide_shift(int n) {
+  int s = 0;
+  while ((1 << s) < n) ++s;
+  return s;
+}
 cudaError_t launch_denoise(int W, int H, const float4* rad, const float* z, const float4* nrm, int iterations,
                            float sigma_z, float sigma_n, float sigma_l, float4* work, float4* out, cudaStream_t s);
 cudaError_t launch_backward_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,

@@ -47,6 +47,23 @@ def test_fp32_mis_frame_matches_oracle(lib, mode):
     assert ok, stats
 
 
+def test_fp32_mis_peaked_env_matches_oracle(lib):
+    # a map with one texel 1e4 times brighter and a band of near-black rows: the texel CDFs have
+    # long plateaus and one large jump, so the cutpoint-guided inversion meets its edge cases
+    cfg = scenegen.CONFIGS["tiny64"]
+    env = scenegen.make_env(cfg.env_h, cfg.env_w, 7).copy()
+    env[3, 5, :3] *= 1e4
+    env[8:12, :, :3] *= 1e-6
+    sc, gb = helpers.scene_arrays(cfg, 1, bias=0.1, n_pixels=600, env=env)
+    out = _render(cfg, sc, gb, sampling=MIS)
+    prm = helpers.oracle_params(sc)
+    opt = helpers.oracle_options(cfg, sampling="mis")
+    ref, allow = orender.render(gb, prm, dataclasses.replace(opt, mis_margin=helpers.MIS_MARGIN))
+    sens = orender.float32_sensitivity(gb, prm, opt, draws=4)
+    ok, stats = helpers.fp32_parity(out[:, :3], ref, sens, extra=allow)
+    assert ok, stats
+
+
 def _bf16_check(cfg, sc, gb, out, offset=0, rows=None, psnr=True, hard=False):
     prm = helpers.oracle_params(sc)
     kw = dict(sampling="mis")
@@ -123,3 +140,27 @@ def test_mis_unsupported_entry_points(lib):
         assert e.value.status == lib.RT_ERR_UNSUPPORTED
     r.sample(dgb["normal"], 1)   # the secondary sampler is unchanged
     torch.cuda.synchronize()
+
+
+def test_bf16_mis_full_size_frame_sampled(lib):
+    # the 800x800, N=128, M=8, L=16, T=2^19 BF16 workload with MIS primary directions, sampled pixels
+    cfg = scenegen.CONFIGS["frame800_bf16"]
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    out = _render(cfg, sc, gb, sampling=MIS)
+    assert np.isfinite(out).all() and np.all(out[:, 3] == 0)
+    rows = scenegen.subset_permutation(cfg.n_pixels, 192, seed=2)
+    _bf16_check(cfg, sc, gb, out, rows=rows, psnr=False)
+
+
+def test_fp32_mis_full_size_frame_sampled(lib):
+    cfg = scenegen.CONFIGS["frame800"]
+    sc, gb = helpers.scene_arrays(cfg, 0)
+    out = _render(cfg, sc, gb, sampling=MIS)
+    assert np.isfinite(out).all()
+    rows = scenegen.subset_permutation(cfg.n_pixels, 96, seed=3)
+    prm = helpers.oracle_params(sc)
+    opt = helpers.oracle_options(cfg, sampling="mis")
+    ref, allow = orender.render(gb, prm, dataclasses.replace(opt, mis_margin=helpers.MIS_MARGIN), rows=rows)
+    sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, draws=4)
+    ok, stats = helpers.fp32_parity(out[rows, :3], ref, sens, extra=allow)
+    assert ok, stats

@@ -95,3 +95,26 @@ def test_multi_light_bf16_against_oracle(lib):
         sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=4, mlp=True)
         ok, stats = helpers.bf16_parity(out[e, :, :3], ref, sens)
         assert ok and stats["psnr_db"] >= helpers.BF16_PSNR_MIN, (e, stats)
+
+
+def test_serve1080_full_size_multi_light_sampled(lib):
+    # the 1920x1080, N=256, M=8, L=16, T=2^20 serving workload: one view, 8 env maps in one call,
+    # in the launch shape the tuner picks; sampled pixels of the first and last light
+    cfg = scenegen.CONFIGS["serve1080"]
+    sc = scenegen.make_scene(cfg, 0)
+    gb = scenegen.make_gbuffer(cfg.n_pixels, 0)
+    envs = _envs(cfg, 8)
+    r = helpers.renderer_for(cfg, sc)
+    dgb = helpers.to_cuda(gb)
+    denv = torch.from_numpy(envs).cuda()
+    r.tune(dgb, denv)
+    out = r.render_frame_multi(dgb, denv).cpu().numpy()
+    assert np.isfinite(out).all() and np.all(out[..., 3] == 0)
+    rows = scenegen.subset_permutation(cfg.n_pixels, 48, seed=4)
+    for e in (0, 7):
+        prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, envs[e])
+        opt = helpers.oracle_options(cfg)
+        ref = orender.render(gb, prm, opt, rows=rows)
+        sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, rel=helpers.BF16_JITTER, draws=4, mlp=True)
+        ok, stats = helpers.bf16_parity(out[e, rows, :3], ref, sens)
+        assert ok, (e, r.launch_shape(), stats)
