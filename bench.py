@@ -105,9 +105,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(cfg, seconds: float, seed: int = 0):
-    """Samples/s of the FP64 oracle on a bounded pixel sample of the workload (host cores)."""
+def cpu_oracle_rate(cfg, seconds: float, seed: int = 0, threads: int = 0):
+    """Samples/s of the FP64 oracle on a bounded pixel sample of the workload (host cores;
+    threads > 0 limits torch's intra-op threads for this call)."""
     import torch
+    if threads > 0:
+        saved = torch.get_num_threads()
+        torch.set_num_threads(threads)
+        try:
+            return cpu_oracle_rate(cfg, seconds, seed)
+        finally:
+            torch.set_num_threads(saved)
     from oracle import render as orender
     sc = scenegen.make_scene(cfg, seed)
     gb = scenegen.make_gbuffer(cfg.n_pixels, seed)
@@ -202,8 +210,8 @@ def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
 # reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_frame800.txt")
 KERNEL_SOURCES = {
-    "bf16": ["render_bf16.cu", "fast_math.cuh", "device_common.cuh", "rt_internal.h"],
-    "fp32": ["render_fp32.cu", "warp_gemm.cuh", "device_common.cuh", "rt_internal.h"],
+    "bf16": ["render_bf16.cu", "fast_math.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
+    "fp32": ["render_fp32.cu", "warp_gemm.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
 }
 
 
@@ -498,6 +506,9 @@ def run_ours(args, cfg):
         rate, done, el, cores = cpu_oracle_rate(cfg, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{done} pixels ({done * cfg.n_dirs} secondary samples) of one 800x800 frame, {el:.1f} s"}
+        r1, d1, e1, _ = cpu_oracle_rate(cfg, max(1.0, args.cpu_seconds / 3), threads=1)
+        cpu["single_core"] = {"value": r1, "unit": UNIT, "cores": 1,
+                              "sample": f"{d1} pixels of the same frame, {e1:.1f} s"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
