@@ -365,9 +365,26 @@ def time_distill(steps: int, warmup: int, barrier, rays: int = 2048, K: int = 10
     t1.record(stream)
     barrier()
     ms = t0.elapsed_time(t1) / steps
+    last = float(loss.sum())
+    # the step's parts, each timed alone with CUDA events on the launching stream (own gradient buffers)
+    scratch_loss = torch.zeros_like(d.loss)
+    scratch_grads = [torch.zeros_like(g) for g in d.grads]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    dirs = student.distill_dirs(rays, K, 0)
+    ev[1].record(stream)
+    feat = teacher.encode(pos)
+    brdf_t = teacher.decode(feat)
+    vis_t, depth_t = teacher.trace(feat, dirs)
+    ev[2].record(stream)
+    student.distill_backward(pos, nrm, dirs, brdf_t, vis_t, depth_t, scratch_loss, *scratch_grads)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    parts = {"dirs": ev[0].elapsed_time(ev[1]), "teacher_stage_kernels": ev[1].elapsed_time(ev[2]),
+             "distill_backward": ev[2].elapsed_time(ev[3])}
     out = {"workload": f"{rays} rays x {K} stratified directions, L=16, T=2^19, fp32 student and teacher",
            "ms_per_step": ms, "value": rays * K / (ms / 1e3), "unit": "ray-direction pairs/s", "steps": steps,
-           "loss_first_last": [first, float(loss.sum())]}
+           "loss_first_last": [first, last], "parts_ms": parts}
     teacher.close()
     student.close()
     return out
@@ -603,7 +620,7 @@ def main():
     ap.add_argument("--no-backward", action="store_true", help="skip the backward (distillation step) timing")
     ap.add_argument("--no-mis", action="store_true", help="skip the MIS-sampling timing")
     ap.add_argument("--no-distill", action="store_true", help="skip the distillation-step timing")
-    ap.add_argument("--mode", choices=["frame", "serve", "backward"], default="frame")
+    ap.add_argument("--mode", choices=["frame", "serve", "backward", "distill"], default="frame")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)
     ap.add_argument("--pixels", type=int, default=0,
@@ -622,6 +639,12 @@ def main():
         torch.cuda.set_device(0)
         line = time_backward(args.steps, args.warmup, torch.cuda.synchronize, rays=args.pixels)
         print(json.dumps({"metric": "backward (distillation step) secondary samples/s", "n_gpus": 1,
+                          "warmup": args.warmup, "dtype": "f32", "data": "synthetic", **line}))
+    elif args.mode == "distill":
+        import torch
+        torch.cuda.set_device(0)
+        line = time_distill(args.steps, args.warmup, torch.cuda.synchronize, rays=args.pixels or 2048)
+        print(json.dumps({"metric": "per-head distillation step, ray-direction pairs/s", "n_gpus": 1,
                           "warmup": args.warmup, "dtype": "f32", "data": "synthetic", **line}))
     else:
         run_ours(args, cfg)

@@ -10,14 +10,18 @@
 //   normalised depth, each averaged over the point's front-facing directions
 //   (w . n > 0) and then over points.
 //
-// Work unit: a warp takes 32 points.  For each of them it encodes f = H(x),
-// counts the front-facing directions and walks the directions 32 at a time
-// (lane = direction): I forward, the head gradients, I's adjoint with the
-// layer-1 f part shared by the rows, then scatters dLoss/df of the I part
-// into the table.  Then the warp runs B on its 32 points as one 32-row tile
-// (lane = point), back-propagates the L1 of the BRDF heads and scatters the
-// B part of dLoss/df.  Weight gradients go to the CTA's shared accumulator
-// (adjoint.cuh) and then to the caller's blobs.
+// Work, in two phases of one persistent launch.  I phase: a unit is one
+// point and up to 128 of its directions; the warp encodes f = H(x), counts
+// the point's front-facing directions and walks the unit's directions 32 at
+// a time (lane = direction): I forward, the head gradients, I's adjoint with
+// the layer-1 f part shared by the rows; then it scatters the unit's share of
+// dLoss/df into the table (the encode adjoint is linear in it).  Splitting a
+// point's directions over units spreads a small batch (2048 points) over
+// every SM.  B phase: a warp takes 32 points as one 32-row tile (lane =
+// point), runs B, back-propagates the L1 of the BRDF heads and scatters the
+// B part of dLoss/df.  I's weight gradients go to the CTA's shared
+// accumulator and then to the caller's blob, B's straight to the caller's
+// blob (adjoint.cuh).
 #include "adjoint.cuh"
 
 namespace rtk {
@@ -25,6 +29,7 @@ namespace rtk {
 namespace {
 
 constexpr int kDW = 5;                      // warps per CTA (shared memory holds one CTA of 5 warps)
+constexpr int kUnitDirs = 128;              // directions of one point per I-phase work unit
 constexpr int kDT = 32 * kDW;
 // per-warp buffers (floats)
 constexpr int DB_F = 0;                                    // f of the warp's 32 points [32 cols]
@@ -92,10 +97,14 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
   const float inv_range = 1.0f / (m.far_t - m.near_t);
   float l_brdf = 0.0f, l_bce = 0.0f, l_depth = 0.0f;
 
-  for (int g0 = (blockIdx.x * kDW + warp) * 32; g0 < P; g0 += gridDim.x * kDW * 32) {
-    // ---- I phase, one point at a time (lane = direction)
-    for (int pr = 0; pr < 32 && g0 + pr < P; ++pr) {
-      const int p = g0 + pr;
+  // ---- I phase: units of (point, up to kUnitDirs of its directions), lane = direction
+  const int nch = (K + kUnitDirs - 1) / kUnitDirs;
+  const long long units = (long long)P * nch;
+  for (long long u = (long long)blockIdx.x * kDW + warp; u < units; u += (long long)gridDim.x * kDW) {
+    {
+      const int p = (int)(u / nch);
+      const int kb = (int)(u - (long long)p * nch) * kUnitDirs;
+      const int ke = min(K, kb + kUnitDirs);
       const f3 x = xyz(pos4[p]);
       const f3 n = xyz(nrm4[p]);
       {
@@ -112,7 +121,6 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
         dfP[lane] = 0.0f;
       }
       __syncwarp();
-      F[aidx(lane, pr)] = fP[lane];   // f of point pr for the B phase (zero beyond L*F)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = lane + 32 * h;
@@ -128,9 +136,9 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
       }
       const float wI = cnt > 0 ? invR / (float)cnt : 0.0f;
       __syncwarp();
-      for (int k0 = 0; k0 < K; k0 += 32) {
+      for (int k0 = kb; k0 < ke; k0 += 32) {
         const int k = k0 + lane;
-        const bool valid = k < K;
+        const bool valid = k < ke;
         const f3 w = valid ? xyz(dirs[(size_t)p * K + k]) : n;
         const bool ff = valid && dot(w, n) > 0.0f;
         float acc[8][8];
@@ -194,18 +202,28 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
         __syncwarp();
       }
       {
+        // the unit's share of dLoss/df (the encode adjoint is linear in it)
         const int l = lane >> 1;
         if ((lane & 1) == 0 && l < levels)
           encode_level_bwd(m.grid, l, x, dfP[lane], dfP[lane + 1], g_table, nullptr);
       }
       __syncwarp();
     }
+  }
 
-    // ---- B phase: the warp's points as one 32-row tile (lane = point)
+  // ---- B phase: groups of 32 points as one 32-row tile (lane = point)
+  for (int g0 = (blockIdx.x * kDW + warp) * 32; g0 < P; g0 += gridDim.x * kDW * 32) {
     const int p = g0 + lane;
     const bool vp = p < P;
-    if (!vp)
-      for (int k = 0; k < 32; ++k) F[aidx(k, lane)] = 0.0f;
+    {
+      const f3 x = vp ? xyz(pos4[p]) : mk(0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int l = 0; l < kMaxLevels; ++l) {
+        const float2 f = (vp && l < levels) ? encode_level(m.grid, l, x) : make_float2(0.f, 0.f);
+        F[aidx(2 * l, lane)] = f.x;
+        F[aidx(2 * l + 1, lane)] = f.y;
+      }
+    }
     __syncwarp();
     float acc[8][8];
     zero(acc);
@@ -323,8 +341,10 @@ cudaError_t launch_distill_dirs(int P, int K, long long ray_offset, uint64_t see
 cudaError_t launch_distill_fp32(const ModelDesc& m, const float4* pos, const float4* nrm, int P, int K,
                                 const float4* dirs, const float* brdf_t, const float* vis_t, const float* depth_t,
                                 float* loss, float* g_table, float* g_brdf, float* g_irt, int num_sms, cudaStream_t s) {
-  const int need = (P + 32 * kDW - 1) / (32 * kDW);
-  const int grid = need < num_sms ? need : num_sms;
+  const long long units = (long long)P * ((K + kUnitDirs - 1) / kUnitDirs);
+  const long long groups = (P + 31) / 32;
+  const long long need = ((units > groups ? units : groups) + kDW - 1) / kDW;
+  const int grid = (int)(need < num_sms ? need : num_sms);
   distill_fp32_kernel<<<grid, kDT, kDSmem, s>>>(m, pos, nrm, P, K, dirs, brdf_t, vis_t, depth_t, loss, g_table,
                                                 g_brdf, g_irt);
   return cudaGetLastError();
