@@ -27,13 +27,14 @@ namespace rtk {
 
 namespace {
 
-constexpr int kBW = 5;                     // warps per CTA
+constexpr int kBW = 6;                     // warps per CTA
 constexpr int kBT = 32 * kBW;
 // per-warp buffers (floats)
 constexpr int WB_F2 = 0;                                   // f' of the chunk's rows  [32 cols]
-constexpr int WB_PE = WB_F2 + kActStride32;                 // PE of the current direction [32 cols]
-constexpr int WB_H1 = WB_PE + kActStride32;                 // layer-1 activations [64 cols]
-constexpr int WB_H2 = WB_H1 + kActStride;                   // layer-2 activations, then dZ2 (in place) [64 cols]
+constexpr int WB_H1 = WB_F2 + kActStride32;                 // layer-1 activations, then dZ1 (in place) [64 cols]
+// PE of the current direction [32 cols] for layer 1, then layer-2 activations and dZ2 (in place)
+// [64 cols]; the PE is written again for the PE part of dW1 once dZ2 is consumed
+constexpr int WB_H2 = WB_H1 + kActStride;
 constexpr int WB_DZ = WB_H2 + kActStride;                  // output gradients [8][32]
 constexpr int WB_FP = WB_DZ + 8 * 32;                       // primary feature f [32]
 constexpr int WB_AP = WB_FP + 32;                           // primary b1 + W1f f [64]
@@ -42,7 +43,7 @@ constexpr int WB_FLOATS = WB_DFP + 32;
 constexpr size_t kBSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kBW * WB_FLOATS) * sizeof(float);
 static_assert(LD_I1 >= 32 + 27 + 1, "gradient rows");
 static_assert(kBSmem <= 232448, "one CTA per SM");
-static_assert(WB_F2 % 4 == 0 && WB_PE % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 &&
+static_assert(WB_F2 % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 &&
                   WB_DZ % 4 == 0 && WB_FLOATS % 4 == 0 && G_FLOATS % 4 == 0,
               "float4 alignment");
 
@@ -110,7 +111,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
   const int rg = lane >> 3, cg = lane & 7;
   float* wb = sg + G_FLOATS + warp * WB_FLOATS;
   float* F2 = wb + WB_F2;
-  float* PEb = wb + WB_PE;
+  float* PEb = wb + WB_H2;   // shares H2's buffer (see WB_H2)
   float* H1 = wb + WB_H1;
   float* H2 = wb + WB_H2;
   float* DZ = wb + WB_DZ;
@@ -269,7 +270,9 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
         __syncwarp();
         bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
         __syncwarp();
+        store_pe(PEb, cosine_direction(n2, m.seed, dir_counter(q, M, 1 + j)), lane);   // again, over dZ2
         bwd_weights(F2, lf, H1, sg + GI_W1, LD_I1, 0, sg + GI_B1, lane);
+        __syncwarp();
         bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, nullptr, lane);
         bwd_input(H1, sw + OFF_IW1F, lf, dF2, lane);
       }
@@ -350,6 +353,8 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       __syncwarp();
       bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
       __syncwarp();
+      store_pe(PEb, wi, lane);   // again, over the consumed dZ2
+      __syncwarp();
       bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
       // the f part of layer 1 is shared by the chunk's rows: dW1f[c][k] += f[k] colsum(dZ1)[c]
       // and dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
@@ -358,19 +363,19 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
         const int c = lane + 32 * h;
         float cs = 0.0f;
         for (int r = 0; r < 32; ++r) cs += H1[aidx(c, r)];
-        H2[c] = cs;   // scratch: column sums of dZ1 (dZ2 is no longer needed)
+        DZ[c] = cs;   // scratch: column sums of dZ1 (the output gradients are consumed)
       }
       __syncwarp();
       for (int k = 0; k < lf; ++k) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = lane + 32 * h;
-          atomicAdd(sg + GI_W1 + c * LD_I1 + k, fP[k] * H2[c]);
+          atomicAdd(sg + GI_W1 + c * LD_I1 + k, fP[k] * DZ[c]);
         }
       }
       if (lane < lf) {
         float s = 0.0f;
-        for (int c = 0; c < 64; ++c) s = fmaf(H2[c], sw[OFF_IW1F + lane * 64 + c], s);
+        for (int c = 0; c < 64; ++c) s = fmaf(DZ[c], sw[OFF_IW1F + lane * 64 + c], s);
         dfP[lane] += s;
       }
       __syncwarp();

@@ -28,14 +28,15 @@ namespace rtk {
 
 namespace {
 
-constexpr int kDW = 5;                      // warps per CTA (shared memory holds one CTA of 5 warps)
+constexpr int kDW = 6;                      // warps per CTA (shared memory holds one CTA of 6 warps)
 constexpr int kUnitDirs = 128;              // directions of one point per I-phase work unit
 constexpr int kDT = 32 * kDW;
 // per-warp buffers (floats)
 constexpr int DB_F = 0;                                    // f of the warp's 32 points [32 cols]
-constexpr int DB_PE = DB_F + kActStride32;                 // PE of the current directions [32 cols]
-constexpr int DB_H1 = DB_PE + kActStride32;                // layer-1 activations [64 cols]
-constexpr int DB_H2 = DB_H1 + kActStride;                  // layer-2 activations, then dZ2 (in place) [64 cols]
+constexpr int DB_H1 = DB_F + kActStride32;                 // layer-1 activations, then dZ1 (in place) [64 cols]
+// PE of the current directions [32 cols] for layer 1, then layer-2 activations and dZ2 (in place)
+// [64 cols]; the PE is written again for the PE part of dW1 once dZ2 is consumed
+constexpr int DB_H2 = DB_H1 + kActStride;
 constexpr int DB_DZ = DB_H2 + kActStride;                 // output gradients [8][32]
 constexpr int DB_FP = DB_DZ + 8 * 32;                      // f of the current point [32]
 constexpr int DB_AP = DB_FP + 32;                          // b1 + W1f f of the current point [64]
@@ -43,7 +44,7 @@ constexpr int DB_DFP = DB_AP + 64;                         // dLoss/df of the cu
 constexpr int DB_FLOATS = DB_DFP + 32;
 constexpr size_t kDSmem = (size_t)(WPACK_FLOATS + G_FLOATS + kDW * DB_FLOATS) * sizeof(float);
 static_assert(kDSmem <= 232448, "one CTA per SM");
-static_assert(DB_PE % 4 == 0 && DB_H1 % 4 == 0 && DB_H2 % 4 == 0 && DB_DZ % 4 == 0 &&
+static_assert(DB_H1 % 4 == 0 && DB_H2 % 4 == 0 && DB_DZ % 4 == 0 &&
                   DB_FLOATS % 4 == 0,
               "float4 alignment");
 
@@ -84,7 +85,7 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
   const int rg = lane >> 3, cg = lane & 7;
   float* wb = sg + G_FLOATS + warp * DB_FLOATS;
   float* F = wb + DB_F;
-  float* PEb = wb + DB_PE;
+  float* PEb = wb + DB_H2;   // shares H2's buffer (see DB_H2)
   float* H1 = wb + DB_H1;
   float* H2 = wb + DB_H2;
   float* DZ = wb + DB_DZ;
@@ -176,6 +177,8 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
         __syncwarp();
         bwd_hidden(H2, sw + OFF_IW2, H1, H1, lane);   // dZ1 over H1, in place
         __syncwarp();
+        store_pe(PEb, w, lane);   // again, over the consumed dZ2
+        __syncwarp();
         bwd_weights(PEb, kPE, H1, sg + GI_W1, LD_I1, lf, sg + GI_B1, lane);
         // the f part of layer 1 is shared by the rows: dW1f[c][k] += f[k] colsum(dZ1)[c],
         // dLoss/df[k] += sum_c colsum(dZ1)[c] W1f[k][c]
@@ -184,19 +187,19 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
           const int c = lane + 32 * h;
           float cs = 0.0f;
           for (int r = 0; r < 32; ++r) cs += H1[aidx(c, r)];
-          H2[c] = cs;   // scratch: column sums of dZ1 (dZ2 is no longer needed)
+          DZ[c] = cs;   // scratch: column sums of dZ1 (the output gradients are consumed)
         }
         __syncwarp();
         for (int kk = 0; kk < lf; ++kk) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
-            atomicAdd(sg + GI_W1 + c * LD_I1 + kk, fP[kk] * H2[c]);
+            atomicAdd(sg + GI_W1 + c * LD_I1 + kk, fP[kk] * DZ[c]);
           }
         }
         if (lane < lf) {
           float s = 0.0f;
-          for (int c = 0; c < 64; ++c) s = fmaf(H2[c], sw[OFF_IW1F + lane * 64 + c], s);
+          for (int c = 0; c < 64; ++c) s = fmaf(DZ[c], sw[OFF_IW1F + lane * 64 + c], s);
           dfP[lane] += s;
         }
         __syncwarp();
