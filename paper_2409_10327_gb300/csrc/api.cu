@@ -341,7 +341,7 @@ rt_status rt_trace(rt_ctx* ctx, const float* feat, const float* dirs, int64_t P,
       depth == nullptr || !aligned(depth, 4))
     return RT_ERR_INVALID_ARG;
   return cuda_status(launch_trace(model_desc(ctx), feat, reinterpret_cast<const float4*>(dirs), (int)P, K, vis,
-                                  depth, (cudaStream_t)stream));
+                                  depth, ctx->num_sms, (cudaStream_t)stream));
 }
 
 rt_status rt_sample(rt_ctx* ctx, const float* normal, int64_t P, int32_t level, int64_t index_offset, float* dirs,

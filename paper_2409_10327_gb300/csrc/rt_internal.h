@@ -118,7 +118,7 @@ cudaError_t launch_encode(const ModelDesc& m, const float4* pos, int P, float* f
                           float* w, cudaStream_t s);
 cudaError_t launch_decode(const ModelDesc& m, const float* feat, int P, float* brdf, cudaStream_t s);
 cudaError_t launch_trace(const ModelDesc& m, const float* feat, const float4* dirs, int P, int K,
-                         float* vis, float* depth, cudaStream_t s);
+                         float* vis, float* depth, int num_sms, cudaStream_t s);
 cudaError_t launch_sample(const ModelDesc& m, const float4* normal, int P, int level, long long offset,
                           float4* dirs, cudaStream_t s);
 cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int level, long long offset,

@@ -1,8 +1,10 @@
 // Stand-alone stage kernels: weight repacking, stage (a) encode, stage (b)
 // decode, stage (c) trace, the direction sampler and stage (e) shading at one
 // level.  They compute exactly what the fused kernel computes per sample and
-// give each stage its own parity check; one thread per output item.
-#include "device_common.cuh"
+// give each stage its own parity check; one thread per output item, except
+// the trace, which also serves the teacher of the distillation step (a point
+// with K directions) and runs as 32-row warp GEMMs.
+#include "warp_gemm.cuh"
 
 namespace rtk {
 
@@ -157,31 +159,77 @@ cudaError_t launch_decode(const ModelDesc& m, const float* feat, int P, float* b
 }
 
 // ---- stage (c) -------------------------------------------------------------
-__global__ void trace_kernel(ModelDesc m, const float* __restrict__ feat, const float4* __restrict__ dirs,
-                             long long PK, int K, float* __restrict__ vis, float* __restrict__ depth) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= PK) return;
-  const long long p = e / K;
-  float f[32];
-  for (int k = 0; k < m.lf; ++k) f[k] = feat[p * m.lf + k];
-  float pe[kPE];
-  positional_encoding(xyz(dirs[e]), [&](int k, float v) { pe[k] = v; });
-  float h2[kHidden];
-  hidden_layers(m.wpack, OFF_IW1F, f, m.lf, OFF_IW1P, pe, kPE, OFF_IB1, OFF_IW2, OFF_IB2, h2);
-  float z0 = __ldg(m.wpack + OFF_IB3), z1 = __ldg(m.wpack + OFF_IB3 + 1);
+// A warp takes one point's directions 32 at a time (lane = direction): the
+// point's layer-1 feature part b1 + W1f f once, then the PE part, layer 2 and
+// the head as in the FP32 frame kernel.  The PE lives in the layer-2 buffer
+// until layer 1 has read it.
+constexpr int kTW = 8;                                    // warps per CTA
+constexpr int kTWFloats = 2 * kActStride + 96;            // H1, PE/H2, f (32), b1 + W1f f (64)
+constexpr size_t kTSmem = (size_t)(WPACK_FLOATS + kTW * kTWFloats) * sizeof(float);
+static_assert(kTSmem <= 232448, "one CTA per SM");
+
+__global__ void __launch_bounds__(kTW * 32, 1)
+trace_kernel(ModelDesc m, const float* __restrict__ feat, const float4* __restrict__ dirs, int P, int K,
+             float* __restrict__ vis, float* __restrict__ depth) {
+  extern __shared__ float4 smem4[];
+  float* sw = reinterpret_cast<float*>(smem4);
+  for (int i = threadIdx.x; i < WPACK_FLOATS / 4; i += kTW * 32)
+    smem4[i] = __ldg(reinterpret_cast<const float4*>(m.wpack) + i);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 3, cg = lane & 7;
+  float* H1 = sw + WPACK_FLOATS + warp * kTWFloats;
+  float* H2 = H1 + kActStride;
+  float* fP = H2 + kActStride;
+  float* aP = fP + 32;
+  const int nch = (K + 31) / 32;
+  const long long units = (long long)P * nch;
+  long long cur = -1;
+  for (long long u = (long long)blockIdx.x * kTW + warp; u < units; u += (long long)gridDim.x * kTW) {
+    const long long p = u / nch;
+    const int k = (int)(u - p * nch) * 32 + lane;
+    if (p != cur) {
+      __syncwarp();
+      fP[lane] = lane < m.lf ? feat[p * m.lf + lane] : 0.0f;
+      __syncwarp();
 #pragma unroll
-  for (int k = 0; k < kHidden; ++k) {
-    z0 = fmaf(h2[k], __ldg(m.wpack + OFF_IW3 + 2 * k), z0);
-    z1 = fmaf(h2[k], __ldg(m.wpack + OFF_IW3 + 2 * k + 1), z1);
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        float acc = sw[OFF_IB1 + c];
+        for (int j = 0; j < m.lfp; ++j) acc = fmaf(fP[j], sw[OFF_IW1F + j * 64 + c], acc);
+        aP[c] = acc;
+      }
+      cur = p;
+    }
+    const bool valid = k < K;
+    const long long e = p * K + k;
+    const f3 w = valid ? xyz(dirs[e]) : mk(0.f, 0.f, 1.f);
+    float acc[8][8];
+    store_pe(H2, w, lane);
+    __syncwarp();
+    zero(acc);
+    warp_gemm<kPEPad>(H2, sw + OFF_IW1P, acc, rg, cg);
+    store_relu_colbias(H1, acc, aP, rg, cg);
+    __syncwarp();
+    zero(acc);
+    warp_gemm<kHidden>(H1, sw + OFF_IW2, acc, rg, cg);
+    store_relu_colbias(H2, acc, sw + OFF_IB2, rg, cg);
+    __syncwarp();
+    const float2 z = irt_head(H2, sw, lane);
+    if (valid) {
+      vis[e] = sigmoidf_(z.x);
+      depth[e] = depth_from_logit(z.y, m.near_t, m.far_t);
+    }
+    __syncwarp();
   }
-  vis[e] = sigmoidf_(z0);
-  depth[e] = depth_from_logit(z1, m.near_t, m.far_t);
 }
 
 cudaError_t launch_trace(const ModelDesc& m, const float* feat, const float4* dirs, int P, int K, float* vis,
-                         float* depth, cudaStream_t s) {
-  const long long PK = (long long)P * K;
-  trace_kernel<<<(unsigned)((PK + 127) / 128), 128, 0, s>>>(m, feat, dirs, PK, K, vis, depth);
+                         float* depth, int num_sms, cudaStream_t s) {
+  const long long units = (long long)P * ((K + 31) / 32);
+  const long long need = (units + kTW - 1) / kTW;
+  const int grid = (int)(need < num_sms ? need : num_sms);
+  trace_kernel<<<grid, kTW * 32, kTSmem, s>>>(m, feat, dirs, P, K, vis, depth);
   return cudaGetLastError();
 }
 
@@ -251,6 +299,7 @@ cudaError_t prepare_kernels() {
   if (e == cudaSuccess) e = prepare_render_bf16();
   if (e == cudaSuccess) e = prepare_backward_fp32();
   if (e == cudaSuccess) e = prepare_distill();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
   return e;
 }
 

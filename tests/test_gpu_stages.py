@@ -71,12 +71,13 @@ def test_decode_matches_oracle(lib):
     np.testing.assert_allclose(out[:, 6], rr.numpy(), atol=2e-6)
 
 
-def test_trace_matches_oracle(lib):
+@pytest.mark.parametrize("P,K", [(300, 5), (40, 70), (3, 1024)])
+def test_trace_matches_oracle(lib, P, K):
+    # few directions per point, a ragged last chunk of 32, and the distillation teacher's K
     cfg = helpers.small_cfg(levels=8)
     sc = scenegen.make_scene(cfg, 6, bias_scale=0.3)
     r = helpers.renderer_for(cfg, sc)
     rng = np.random.default_rng(7)
-    P, K = 300, 5
     feat = rng.normal(0, 0.2, (P, 16)).astype(np.float32)
     d = rng.normal(size=(P, K, 3))
     d /= np.linalg.norm(d, axis=-1, keepdims=True)
