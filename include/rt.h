@@ -101,9 +101,11 @@ typedef struct rt_config {
                             (texel probability ~ max(0, luminance) + 1e-6, point
                             uniform in (phi, theta) inside the texel) with (u1,
                             u2).  Secondary directions stay cosine-weighted.
-                            Render calls only (rt_render_frame[_multi], rt_tune);
-                            rt_sample / rt_shade at level 0, rt_backward and
-                            rt_render_frame_static return RT_ERR_UNSUPPORTED.
+                            Render calls (rt_render_frame[_multi], rt_tune) and
+                            rt_backward, where the draws and their weights are
+                            constants of the estimator; rt_sample / rt_shade at
+                            level 0 and rt_render_frame_static return
+                            RT_ERR_UNSUPPORTED.
                             Multi-light renders draw from the bound map's
                             distribution for every light (unbiased for each). */
   int32_t env_h, env_w;  /* environment map size, each 1..8192                  */

@@ -491,7 +491,7 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
   rt_status st = check_ctx(ctx);
   if (st != RT_OK) return st;
   if (P < 0 || P > kMaxP || pixel_offset < 0) return RT_ERR_INVALID_ARG;
-  if (ctx->cfg.visibility == RT_VIS_HARD || ctx->cfg.sampling == RT_SAMPLE_MIS) return RT_ERR_UNSUPPORTED;
+  if (ctx->cfg.visibility == RT_VIS_HARD) return RT_ERR_UNSUPPORTED;
   if (P == 0) return RT_OK;
   if (!check_gbuffer(gb) || !check_plane(d_radiance) || g_table == nullptr || !aligned(g_table, 8) ||
       g_brdf == nullptr || !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))

@@ -22,6 +22,7 @@
 // per-CTA shared-memory accumulator (padded rows, shared atomics), which the
 // CTA adds to the caller's gradient blobs once at the end.
 #include "adjoint.cuh"
+#include "mis.cuh"
 
 namespace rtk {
 
@@ -161,7 +162,9 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       const int i = i0 + lane;
       const bool valid = i < N;
       const uint64_t q = (uint64_t)(pixel_offset + pix) * (uint64_t)N + (uint64_t)i;
-      const f3 wi = cosine_direction(n, m.seed, dir_counter(q, M, 0));
+      // the primary direction and its Eq. 1 factor are constants of the estimator (MIS included)
+      const f3 wi = m.mis ? mis_direction(m, n, wo, ar.w, i, dir_counter(q, M, 0))
+                          : cosine_direction(n, m.seed, dir_counter(q, M, 0));
       float acc[8][8];
 
       // ---- forward of I(f, w_i)
@@ -215,7 +218,8 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
 
       // ---- primary shading factors and the incoming-radiance gradient
       const f3 e1 = env_lookup(m.env, m.env_h, m.env_w, wi);
-      const f3 fr1 = brdf_eval(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
+      const f3 fr1 = m.mis ? mis_weighted_brdf(m, xyz(ar), ar.w, n, wo, wi)
+                           : brdf_eval(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       const float sN = kPi / (float)N, sM = kPi / (float)M;
       const f3 dli = valid ? (G * fr1) * sN : mk(0.f, 0.f, 0.f);
       const f3 dlo2 = dli * (1.0f - v);

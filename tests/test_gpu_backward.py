@@ -105,7 +105,8 @@ def test_backward_matches_fp64_gradient_on_256_rays(lib):
 
 @pytest.mark.parametrize("modes,ov", [({"lambert": True}, {"brdf_mode": 1}),
                                       ({"force_vis": 0.0}, {"force_vis": 0.0}),
-                                      ({"force_vis2": 1.0}, {"force_vis2": 1.0})])
+                                      ({"force_vis2": 1.0}, {"force_vis2": 1.0}),
+                                      ({"sampling": "mis"}, {"sampling": 1})])
 def test_backward_modes(lib, modes, ov):
     cfg = helpers.small_cfg(n_dirs=32, m_dirs=4, levels=6, log2_T=12, max_res=128)
     sc, gb, up, ref = _case(cfg, 48, **modes)
