@@ -112,7 +112,7 @@ def distill_gradient(x, n, w, student: Params, targets, opt):
     total, terms = distill_loss(x, n, w, p, targets, opt)
     total.backward()
     flat = lambda layers: torch.cat([torch.cat([a.grad.reshape(-1), b.grad.reshape(-1)]) for a, b in layers])
-    return [float(t) for t in terms], tab.grad, flat(brdf), flat(irt)
+    return [float(t.detach()) for t in terms], tab.grad, flat(brdf), flat(irt)
 
 
 def adam_step(p, g, m, v, step: int, lr=2e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
