@@ -18,9 +18,12 @@
 //      dz0 from dv = dL_i . (Lenv(w_i) - L'_o,i), and back-propagates the
 //      primary I (recomputed) into its weights and into dLoss/df.
 // After the pixel's last chunk the primary encode scatters dLoss/df into the
-// table.  Weight gradients of each chunk are small warp GEMMs added to a
-// per-CTA shared-memory accumulator (padded rows, shared atomics), which the
-// CTA adds to the caller's gradient blobs once at the end.
+// table.  Weight gradients of each chunk are small warp GEMMs.  I's (1 + M
+// evaluations per chunk) are added to a per-CTA shared-memory accumulator
+// (padded rows, shared atomics) that the CTA adds to the caller's blob once at
+// the end; B's (one evaluation per chunk) go to the caller's blob directly.
+// With MIS primary directions (Sec. 4.1) each draw and its weight are
+// constants too; only w_i and its Eq. 1 factor change.
 #include "adjoint.cuh"
 #include "mis.cuh"
 
