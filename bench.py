@@ -406,7 +406,10 @@ def run_ours(args, cfg):
 
     from paper_2409_10327_gb300.parallel import max_over_ranks
 
-    renderers, gbs = _setup(cfg, rank)
+    from paper_2409_10327_gb300 import binding
+    main_modes = {"visibility": binding.RT_VIS_HARD if args.visibility == "hard" else binding.RT_VIS_SOFT,
+                  "sampling": binding.RT_SAMPLE_MIS if args.sampling == "mis" else binding.RT_SAMPLE_COSINE}
+    renderers, gbs = _setup(cfg, rank, **main_modes)
     out = torch.empty(cfg.n_pixels, 4, device="cuda")
     total_ms, launch_ms, clk = _time_frames(renderers, gbs, out, args.steps, args.warmup, barrier,
                                             ClockSampler(local))
@@ -531,7 +534,8 @@ def run_ours(args, cfg):
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if cfg.precision == "fp32" else "bf16",
             "data": "synthetic",
-            "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": 4},
+            "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": 4,
+                       "visibility": args.visibility, "sampling": args.sampling},
             "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
@@ -621,6 +625,10 @@ def main():
     ap.add_argument("--no-mis", action="store_true", help="skip the MIS-sampling timing")
     ap.add_argument("--no-distill", action="store_true", help="skip the distillation-step timing")
     ap.add_argument("--mode", choices=["frame", "serve", "backward", "distill"], default="frame")
+    ap.add_argument("--visibility", choices=["soft", "hard"], default="soft",
+                    help="visibility of the main frame leg (the headline is soft)")
+    ap.add_argument("--sampling", choices=["cosine", "mis"], default="cosine",
+                    help="primary directions of the main frame leg (the headline is cosine)")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)
     ap.add_argument("--pixels", type=int, default=0,
