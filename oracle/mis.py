@@ -49,6 +49,8 @@ import math
 import numpy as np
 import torch
 
+from . import shading
+
 LUMA32 = np.array([0.2126, 0.7152, 0.0722], np.float32)
 LUM_FLOOR32 = np.float32(1e-6)
 NOV_MIN = 1e-4
@@ -193,9 +195,7 @@ def pdf_ggx(w: torch.Tensor, n: torch.Tensor, wo: torch.Tensor, alpha: torch.Ten
     noh = (n * h).sum(-1)
     voh = (wo * h).sum(-1)
     a2 = alpha * alpha
-    c = torch.cross(n, h, dim=-1)
-    dd = (c * c).sum(-1) + noh * noh * a2          # (n.h)^2 (a2 - 1) + 1 on the unit sphere
-    d = a2 / (math.pi * dd * dd)
+    d = shading.ggx_d(torch.clamp(noh, min=0.0), a2)
     nov_c = torch.clamp(nov, min=NOV_MIN)
     g1 = 2.0 * nov_c / (nov_c + torch.sqrt(a2 + (1.0 - a2) * nov_c * nov_c))
     ok = (nov > NOV_MIN) & (noh > 0) & (voh > 0) & (hl > 0)

@@ -111,10 +111,19 @@ class Params:
 
 
 def _gbuffer_tensors(gb: Dict[str, np.ndarray], rows: np.ndarray):
+    """(x, n, w_o, albedo, roughness) of G-buffer rows in float64.
+
+    The paper's n and w_o are unit vectors; the G-buffer holds them rounded
+    to float32, so the oracle takes the unit vectors those triples denote
+    (normalised in float64).
+    """
     def g(key, k):
         return torch.from_numpy(np.asarray(gb[key][rows, :k], np.float64))
+
+    def unit(v):
+        return v / v.norm(dim=-1, keepdim=True).clamp(min=1e-300)
     ar = torch.from_numpy(np.asarray(gb["albedo_rough"][rows], np.float64))
-    return g("pos", 3), g("normal", 3), g("view", 3), ar[:, :3], ar[:, 3]
+    return g("pos", 3), unit(g("normal", 3)), unit(g("view", 3)), ar[:, :3], ar[:, 3]
 
 
 def _primary_dirs(x, n, wo, rough, q, prm: Params, opt: Options, jitter=None):

@@ -19,7 +19,10 @@ BRDF (Sec. 3.1 "simplified Disney model"; Sec. 4.1; Sec. 4.2 teacher; Sec. 5):
   NoL = max(n.w_i, 0), NoV = max(n.w_o, 1e-4), n.h clamped at 0.
 Readings: no normal flipping; the specular term is grey (F0 scalar);
 h = (w_i + w_o)/|w_i + w_o| with w_o.h = |w_i + w_o| / 2; a degenerate
-half vector (|w_i + w_o|^2 <= 1e-20) gives n.h = 0.
+half vector (|w_i + w_o|^2 <= 1e-20) gives n.h = 0.  Every direction and
+normal reaching brdf() is a unit vector in float64 (render.py normalises
+the G-buffer's n and w_o, B's n' and the sampled directions), so D is the
+textbook form above.
 
 Monte Carlo sums with cosine-weighted directions, p(w) = (w.n) / pi, so the
 cosine over the pdf in Eq. 1 is pi:
@@ -34,7 +37,12 @@ Pins (tests/test_oracle_shading.py): constant and linear env maps, exact
 texel centres and seam continuity; D integrates to 1 against n.h over the
 sphere (quadrature); Vis equals the textbook height-correlated
 G2 = 1 / (1 + Lambda(w_o) + Lambda(w_i)) divided by 4 NoL NoV; Schlick's end
-points; the white furnace (render tests).
+points; and brdf() itself: its peak F0 / (4 pi alpha^2) at normal incidence,
+agreement with the microfacet model written in angles (D from tan theta_h,
+G2 from Lambda, w_o.h from half the angle between w_i and w_o), the closed-
+form directional albedo 1 - mu ln(1 + 1/mu) of the alpha = 1, F = 1 lobe,
+and the white-furnace energy of the GGX-Smith lobe against quadrature of
+that angle form; the white furnace of the whole estimator (render tests).
 """
 from __future__ import annotations
 
@@ -69,7 +77,7 @@ def env_lookup(env: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
 
 
 def ggx_d(noh: torch.Tensor, a2: torch.Tensor) -> torch.Tensor:
-    """GGX normal distribution with alpha^2 = a2 (unit vectors; brdf() uses the |n x h|^2 form)."""
+    """GGX normal distribution D(h) = a2 / (pi ((n.h)^2 (a2 - 1) + 1)^2), alpha^2 = a2, unit vectors."""
     return a2 / (math.pi * (noh * noh * (a2 - 1.0) + 1.0) ** 2)
 
 
@@ -103,15 +111,10 @@ def brdf(albedo: torch.Tensor, rough: torch.Tensor, n: torch.Tensor, wi: torch.T
     ok = hl2 > 1e-20
     hl = torch.sqrt(torch.where(ok, hl2, torch.ones_like(hl2)))
     h = hv / hl[..., None]
-    noh_raw = torch.where(ok, (n * h).sum(-1), torch.zeros_like(hl))
-    noh = noh_raw.clamp(min=0.0)
+    # n.h clamped at 0 (D = a2 / pi there); a degenerate half vector gives n.h = 0 and w_o.h = 0
+    noh = torch.where(ok, (n * h).sum(-1), torch.zeros_like(hl)).clamp(min=0.0)
     voh = torch.where(ok, 0.5 * hl, torch.zeros_like(hl))
-    # GGX D with 1 - (n.h)^2 written as |n x h|^2 (equal for unit vectors; the same
-    # expression as the GGX sampling density, so that D cancels between the two
-    # on inputs that are unit only to float32 rounding); D = a2 / pi where n.h <= 0
-    c = torch.cross(n.expand_as(h), h, dim=-1)
-    dd = torch.where(ok & (noh_raw > 0), (c * c).sum(-1) + noh * noh * a2, torch.ones_like(hl))
-    spec = a2 / (math.pi * dd * dd) * schlick_fresnel(voh, f0) * smith_vis(nol, nov, a2)
+    spec = ggx_d(noh, a2) * schlick_fresnel(voh, f0) * smith_vis(nol, nov, a2)
     return diffuse + spec[..., None]
 
 
