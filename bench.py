@@ -105,15 +105,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(cfg, seconds: float, seed: int = 0, threads: int = 0):
+def host_cpu() -> dict:
+    """The host's logical CPU count and model name (lscpu; /proc/cpuinfo as a fallback)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def cpu_oracle_rate(cfg, seconds: float, seed: int = 0, threads: int = 0, keep: bool = False):
     """Samples/s of the FP64 oracle on a bounded pixel sample of the workload (host cores;
-    threads > 0 limits torch's intra-op threads for this call)."""
+    threads > 0 limits torch's intra-op threads for this call).  Returns (samples/s, pixels,
+    seconds, threads) and, with keep=True, also the rendered rows and their radiance."""
     import torch
     if threads > 0:
         saved = torch.get_num_threads()
         torch.set_num_threads(threads)
         try:
-            return cpu_oracle_rate(cfg, seconds, seed)
+            return cpu_oracle_rate(cfg, seconds, seed, keep=keep)
         finally:
             torch.set_num_threads(saved)
     from oracle import render as orender
@@ -124,13 +144,52 @@ def cpu_oracle_rate(cfg, seconds: float, seed: int = 0, threads: int = 0):
     rows = scenegen.subset_permutation(cfg.n_pixels, cfg.n_pixels, seed=1)
     chunk = max(1, (1 << 15) // cfg.n_dirs)
     done, t0 = 0, time.perf_counter()
+    outs = []
     while True:
-        orender.render(gb, prm, opt, rows=rows[done:done + chunk])
+        o = orender.render(gb, prm, opt, rows=rows[done:done + chunk])
+        if keep:
+            outs.append(o)
         done += chunk
         el = time.perf_counter() - t0
         if el >= seconds or done >= cfg.n_pixels:
             break
-    return done * cfg.n_dirs / el, done, el, torch.get_num_threads()
+    done = min(done, cfg.n_pixels)
+    res = (done * cfg.n_dirs / el, done, el, torch.get_num_threads())
+    if keep:
+        return res + (rows[:done], np.concatenate(outs, axis=0)[:done])
+    return res
+
+
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_frame_stats(cfg, seed: int):
+    """(peak, p99.9) of the whole FP64 oracle frame from tests/golden, or None."""
+    path = os.path.join(GOLDEN_DIR, f"{cfg.name.split('[')[0].replace('_bf16', '')}_seed{seed}_stats.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if not line.startswith("#") and len(line.split()) == 2:
+            kv[line.split()[0]] = float(line.split()[1])
+    return (kv["peak"], kv["p999"]) if "peak" in kv and "p999" in kv else None
+
+
+def parity_stats(got: np.ndarray, ref: np.ndarray, precision: str, peaks=None) -> dict:
+    """Errors of a rendered sample against the FP64 oracle's radiance of the same pixels."""
+    err = np.abs(got - ref)
+    amax = float(np.abs(ref).max()) if ref.size else 1.0
+    rel = err / np.maximum(np.abs(ref), 1e-6 * amax)
+    st = {"pixels": int(ref.shape[0]), "frame_rel_l1": float(err.sum() / max(np.abs(ref).sum(), 1e-300)),
+          "max_abs": float(err.max()), "max_rel": float(rel.max()), "median_rel": float(np.median(rel))}
+    if precision == "bf16":
+        mse = float((err ** 2).mean())
+        peak, p999 = peaks if peaks is not None else (amax, float(np.quantile(ref, 0.999)))
+        st["psnr_db_peak_max"] = 10.0 * math.log10(peak * peak / mse) if mse > 0 else float("inf")
+        st["psnr_db_peak_p999"] = 10.0 * math.log10(p999 * p999 / mse) if mse > 0 else float("inf")
+        st["peaks"] = {"max": peak, "p999": p999,
+                       "source": "whole-frame FP64 oracle (tests/golden)" if peaks is not None else "the sample"}
+    return st
 
 
 def run_reference(args, cfg):
@@ -210,7 +269,7 @@ def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
 # reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_frame800.txt")
 KERNEL_SOURCES = {
-    "bf16": ["render_bf16.cu", "fast_math.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
+    "bf16": ["render_bf16.cu", "fast_math.cuh", "mis.cuh", "mbarrier.cuh", "device_common.cuh", "rt_internal.h"],
     "fp32": ["render_fp32.cu", "warp_gemm.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
 }
 
@@ -239,25 +298,100 @@ def measured_traffic(cfg):
     return None
 
 
-def _roofline(cfg, launch_ms, peaks):
+def measured_l2_sectors_per_sample(cfg):
+    """L2 sectors read per secondary sample by the frame kernel (ncu lts__t_sectors_srcunit_tex_op_read
+    over a capture, divided by its samples), recorded beside the traffic for the current sources, or None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    want = kernel_source_hash(cfg.precision)
+    for line in open(TRAFFIC_FILE):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(item.split("=", 1) for item in line.split())
+        if kv.get("precision") == cfg.precision and kv.get("source_sha256") == want and "l2_sectors_per_sample" in kv:
+            return float(kv["l2_sectors_per_sample"])
+    return None
+
+
+def measure_probe_peaks(table_bytes: int = 32 << 20, reps: int = 5) -> dict:
+    """Live ceilings from the library's probe kernels, timed with CUDA events on the current stream:
+    random 4- and 8-byte gathers over an L2-resident table of the FP16 frame table's size (32 MiB), and
+    FP32 FMA throughput.  Each figure is the best of `reps` launches after two warm-ups (a burst rate)."""
+    import torch
+    from paper_2409_10327_gb300 import binding
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = 4 * sms                     # 2048 threads per SM
+    stream = torch.cuda.current_stream()
+    table = torch.randint(0, 1 << 30, (table_bytes // 4,), dtype=torch.int32, device="cuda")
+    sink = torch.empty(blocks * 512, dtype=torch.float32, device="cuda")
+    isink = sink.view(torch.int32)
+
+    def best_ms(fn):
+        for _ in range(2):
+            fn()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        return min(times)
+    out = {"how": f"rt_probe_gather / rt_probe_ffma, {blocks} blocks x 512 threads, best of {reps} after 2 warm-ups"}
+    iters = 512
+    for bpl in (4, 8):
+        ms = best_ms(lambda: binding.probe_gather(table, bpl, iters, blocks, sink=isink))
+        loads = blocks * 512 * iters * 8
+        out[f"l2_gather_{bpl}B"] = {"table_MiB": table_bytes >> 20, "ms": ms, "loads_per_s": loads / (ms / 1e3),
+                                    "useful_GBps": loads * bpl / (ms / 1e3) / 1e9}
+    f_iters = 4096
+    ms = best_ms(lambda: binding.probe_ffma(f_iters, blocks, sink=sink))
+    out["ffma_tflops"] = blocks * 512 * f_iters * 256 / (ms / 1e3) / 1e12
+    out["ffma_ms"] = ms
+    del table, sink
+    return out
+
+
+def _roofline(cfg, launch_ms, peaks, probes=None):
     flop = algorithmic_flop_per_sample(cfg) * cfg.samples
     avg_s = sum(launch_ms) / len(launch_ms) / 1e3
     if cfg.precision == "fp32":
-        roof = {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}
+        if probes and probes.get("ffma_tflops"):
+            roof = {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": probes["ffma_tflops"], "unit": "TFLOP/s",
+                    "peak_source": "of measured (rt_probe_ffma, burst, same run)"}
+        else:
+            roof = {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"}
     else:
-        pk = peaks.get("bf16_tflops_sustained")
-        roof = {"bound": "tensor", "achieved": flop / avg_s / 1e12, "peak": pk if pk else 1700.0, "unit": "TFLOP/s",
-                "peak_source": "of measured (bf16_tflops_sustained)" if pk else "of fallback"}
+        # one launch of tens of ms timed alone is a burst: the burst cuBLAS figure is its denominator
+        pk = peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "achieved": flop / avg_s / 1e12, "peak": pk if pk else 1900.0, "unit": "TFLOP/s",
+                "peak_source": "of measured (bf16_tflops, burst)" if pk else "of fallback (1.9 PFLOP/s burst)"}
+        if peaks.get("bf16_tflops_sustained"):
+            roof["frac_of_sustained"] = roof["achieved"] / peaks["bf16_tflops_sustained"]
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(cfg)
     roof["algorithmic_per_launch"] = flop
     roof["kernel_ms"] = avg_s * 1e3
-    gather_bytes = cfg.samples * cfg.levels * 8 * (4 if cfg.precision == "bf16" else 8)
+    bpl = 4 if cfg.precision == "bf16" else 8          # bytes of one table entry (one hash-grid corner)
+    gather_bytes = cfg.samples * cfg.levels * 8 * bpl
+    corners_per_s = cfg.samples * cfg.levels * 8 / avg_s
     hbm = peaks.get("hbm_gbs")
-    roof["gather"] = {"algorithmic_bytes_per_launch": gather_bytes, "achieved_GBps": gather_bytes / avg_s / 1e9,
-                      "hbm_peak_GBps": hbm, "frac_of_hbm": (gather_bytes / avg_s / 1e9 / hbm) if hbm else None,
-                      "note": "table is L2-resident; the scattered-gather limit is L1TEX wavefronts"}
+    g = {"algorithmic_bytes_per_launch": gather_bytes, "algorithmic_bytes_per_sample": cfg.levels * 8 * bpl,
+         "achieved_GBps": gather_bytes / avg_s / 1e9, "hbm_peak_GBps": hbm,
+         "frac_of_hbm": (gather_bytes / avg_s / 1e9 / hbm) if hbm else None}
+    probe = (probes or {}).get(f"l2_gather_{bpl}B")
+    if probe:
+        # the table is L2-resident, so the binding roof is the L2 random-gather rate of loads this size
+        g["l2_gather_peak_GBps"] = probe["useful_GBps"]
+        g["frac_of_l2_gather"] = gather_bytes / avg_s / 1e9 / probe["useful_GBps"]
+        g["corner_loads_per_s"] = corners_per_s
+        sectors = measured_l2_sectors_per_sample(cfg)
+        if sectors is not None:
+            g["l2_sectors_per_sample"] = sectors
+            g["l2_sector_rate_frac"] = sectors * cfg.samples / avg_s / probe["loads_per_s"]
+    roof["gather"] = g
     return roof
 
 
@@ -390,6 +524,63 @@ def time_distill(steps: int, warmup: int, barrier, rays: int = 2048, K: int = 10
     return out
 
 
+def backward_gradient_check(n_rays: int = 256) -> dict:
+    """The FP64 oracle's gradient of the L2 distillation loss on the 256-ray check subset of the
+    differentiation workload (timed on the host cores: the backward's CPU baseline), against the
+    GPU adjoint's gradient on the same rays: per-tensor ||g - g_ref|| / ||g_ref|| and cosine."""
+    import torch
+    from oracle import render as orender
+    from paper_2409_10327_gb300 import binding
+    cfg = scenegen.CONFIGS["grad65k"]
+    student = scenegen.make_scene(cfg, 2, bias_scale=0.1)
+    teacher = scenegen.make_scene(cfg, 1, bias_scale=0.1)
+    full = scenegen.make_gbuffer(cfg.n_pixels, 3)
+    rows = np.sort(scenegen.subset_permutation(cfg.n_pixels, n_rays, seed=0))
+    gb = {k: np.ascontiguousarray(v[rows]) for k, v in full.items()}
+    opt = orender.Options.from_config(cfg)
+    idx = np.arange(n_rays)
+    t0 = time.perf_counter()
+    t_prm = orender.Params.from_arrays(teacher.table, teacher.brdf, teacher.irt, student.env)
+    s_prm = orender.Params.from_arrays(student.table, student.brdf, student.irt, student.env, requires_grad=True)
+    with torch.no_grad():
+        target = orender.render(gb, t_prm, opt, rows=idx)
+        l_s = orender.render(gb, orender.Params.from_arrays(student.table, student.brdf, student.irt, student.env),
+                             opt, rows=idx)
+    up = orender.upstream_gradient(l_s, target)
+    _, g_table, g_brdf, g_irt = orender.distill_gradient(gb, idx, s_prm, torch.from_numpy(target), opt)
+    el = time.perf_counter() - t0
+    r = binding.Renderer(binding.make_config(cfg))
+    r.set_params(torch.from_numpy(student.table).cuda(), torch.from_numpy(student.brdf_blob).cuda(),
+                 torch.from_numpy(student.irt_blob).cuda(), torch.from_numpy(student.env).cuda())
+    dgb = {k: torch.from_numpy(v).cuda() for k, v in gb.items()}
+    g4 = torch.zeros(n_rays, 4, device="cuda")
+    g4[:, :3] = torch.from_numpy(up.astype(np.float32)).cuda()
+    gt = torch.zeros(student.table.shape, device="cuda")
+    gbw = torch.zeros(student.brdf_blob.size, device="cuda")
+    giw = torch.zeros(student.irt_blob.size, device="cuda")
+    r.backward(dgb, g4, gt, gbw, giw)
+    torch.cuda.synchronize()
+    r.close()
+    lf = cfg.levels * 2
+    parts = {"table": (gt.cpu().numpy(), g_table.numpy())}
+    for name, got, ref, ind, outd in (("brdf", gbw.cpu().numpy(), g_brdf.numpy(), lf, 7),
+                                      ("irt", giw.cpu().numpy(), g_irt.numpy(), lf + 27, 2)):
+        for k, ((wg, bg), (wr, br)) in enumerate(zip(scenegen.unpack_mlp(got, ind, outd),
+                                                     scenegen.unpack_mlp(ref, ind, outd))):
+            parts[f"{name}.W{k + 1}"] = (wg, wr)
+            parts[f"{name}.b{k + 1}"] = (bg, br)
+    stats = {}
+    for k, (a, b) in parts.items():
+        nb = float(np.linalg.norm(b))
+        if nb > 0:
+            stats[k] = {"relnorm": float(np.linalg.norm(a.ravel() - b.ravel()) / nb),
+                        "cosine": float(np.dot(a.ravel(), b.ravel()) / max(np.linalg.norm(a) * nb, 1e-300))}
+    return {"rays": n_rays, "reference": "FP64 oracle autograd gradient (directions held fixed)",
+            "per_tensor": stats, "max_relnorm": max(v["relnorm"] for v in stats.values()),
+            "cpu_baseline": {"value": n_rays * cfg.n_dirs / el, "unit": "ray-direction samples/s", "seconds": el,
+                             "kind": "oracle", "sample": f"{n_rays} rays x {cfg.n_dirs} directions (forward + gradient)"}}
+
+
 def run_ours(args, cfg):
     import dataclasses
     import torch
@@ -436,6 +627,10 @@ def run_ours(args, cfg):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     h2d = sum(v.numel() * v.element_size() for v in host_gb[0].values())
     d2h = host_out.numel() * host_out.element_size()
+    # scene 0's frame in the timed launch configuration, kept for the parity block
+    frames = {cfg.precision: renderers[0].render_frame(gbs[0]).cpu().numpy()[:, :3]}
+    # live ceilings for the rooflines: L2 random-gather rates and FP32 FMA throughput
+    probes = measure_probe_peaks()
 
     # the spatial SVGF denoiser (Sec. 4.1) on the rendered frame; depth = distance to a camera at (0, 0, -3)
     den = None
@@ -471,7 +666,9 @@ def run_ours(args, cfg):
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
         compare = {"precision": other.precision, "value": world * other.samples * steps / (o_total / 1e3),
                    "unit": UNIT, "ms_per_frame": o_total / steps, "steps": steps,
-                   "roofline": _roofline(other, o_launch, peaks)}
+                   "roofline": _roofline(other, o_launch, peaks, probes)}
+        if args.visibility == "soft" and args.sampling == "cosine":
+            frames[other.precision] = rs[0].render_frame(gs[0]).cpu().numpy()[:, :3]
         for r in rs:
             r.close()
 
@@ -513,6 +710,12 @@ def run_ours(args, cfg):
     # row a10: one distillation step (forward + hand-written adjoint)
     bwd = None if args.no_backward else time_backward(max(3, args.steps // 4), args.warmup, barrier)
     dst = None if args.no_distill else time_distill(max(3, args.steps // 4), args.warmup, barrier)
+    if bwd is not None:
+        r = bwd["roofline"]
+        r["peak"], r["frac"] = probes["ffma_tflops"], r["achieved"] / probes["ffma_tflops"]
+        r["peak_source"] = "of measured (rt_probe_ffma, burst, same run)"
+    # batched serving (16 views x 8 lights at 1920x1080, one CUDA graph per batch)
+    srv = None if args.no_serve else time_serve(args.views, args.lights, args.serve_steps, 1, rank, local)
 
     if rank != 0:
         if world > 1:
@@ -522,13 +725,22 @@ def run_ours(args, cfg):
 
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     cpu = None
+    parity = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, done, el, cores = cpu_oracle_rate(cfg, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+        # the oracle timed on the host cores; the pixels it renders (a seeded sample of scene 0, the
+        # first timed scene) are also the reference of the parity block
+        rate, done, el, cores, rows, ref = cpu_oracle_rate(cfg, args.cpu_seconds, keep=True)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
                "sample": f"{done} pixels ({done * cfg.n_dirs} secondary samples) of one 800x800 frame, {el:.1f} s"}
         r1, d1, e1, _ = cpu_oracle_rate(cfg, max(1.0, args.cpu_seconds / 3), threads=1)
         cpu["single_core"] = {"value": r1, "unit": UNIT, "cores": 1,
                               "sample": f"{d1} pixels of the same frame, {e1:.1f} s"}
+        if args.visibility == "soft" and args.sampling == "cosine" and cfg.n_pixels == 800 * 800:
+            parity = {"reference": f"FP64 oracle, the same {done} seeded pixels of scene 0 as cpu_baseline",
+                      **{prec: parity_stats(fr[rows], ref, prec, golden_frame_stats(cfg, 0) if prec == "bf16" else None)
+                         for prec, fr in frames.items()}}
+        if bwd is not None and not args.no_grad_check:
+            bwd["gradient_check"] = backward_gradient_check()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
@@ -536,7 +748,8 @@ def run_ours(args, cfg):
             "data": "synthetic",
             "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": 4,
                        "visibility": args.visibility, "sampling": args.sampling},
-            "roofline": _roofline(cfg, launch_ms, peaks), "cpu_baseline": cpu,
+            "roofline": _roofline(cfg, launch_ms, peaks, probes), "cpu_baseline": cpu, "parity": parity,
+            "probes": probes, "serve": srv,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": args.steps, "clocks": clk, "compare": compare, "hard_visibility": hard, "mis": mis_line, "denoise": den, "backward": bwd, "distill": dst,
@@ -548,17 +761,13 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
-def run_serve(args):
-    """Batched serving: V views x E lights at 1920x1080 (N=256, L=16, T=2^20, BF16), one CUDA-graph launch."""
+def time_serve(views: int, lights: int, steps: int, warmup: int, rank: int = 0, local: int = 0) -> dict:
+    """Batched serving: V views x E lights at 1920x1080 (N=256, L=16, T=2^20, BF16), one CUDA-graph launch
+    per batch after rt_tune picked the launch shape; per-view latencies from events inside the graph."""
     import torch
-    rank, local, world = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     from paper_2409_10327_gb300 import binding, serve
     cfg = scenegen.CONFIGS["serve1080"]
-    V, E = args.views, args.lights
+    V, E = views, lights
     sc = scenegen.make_scene(cfg, 0)
     r = binding.Renderer(binding.make_config(cfg))
     r.set_params(torch.from_numpy(sc.table).cuda().half(), torch.from_numpy(sc.brdf_blob).cuda(),
@@ -570,7 +779,7 @@ def run_serve(args):
     tuned_ms = srv.tune()
     shape = r.launch_shape()
     srv.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         srv.replay()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -579,31 +788,51 @@ def run_serve(args):
     t1 = torch.cuda.Event(enable_timing=True)
     lats = []
     t0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         srv.replay()
         t1.record()
         torch.cuda.synchronize()
         lats += srv.view_latencies_ms()
     clk = clocks.stop()
     total_ms = t0.elapsed_time(t1)
-    frames = V * E * args.steps
-    samples = cfg.samples * V * args.steps          # secondary samples of the geometry passes
+    frames = V * E * steps
+    samples = cfg.samples * V * steps          # secondary samples of the geometry passes
     lat = np.array(lats)
+    out = {"workload": f"serve1080: {V} views x {E} env maps, 1920x1080, N=256, M=8, L=16, T=2^20, bf16",
+           "value": samples / (total_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_batch": total_ms / steps, "frames_per_s": frames / (total_ms / 1e3),
+           "lit_samples_per_s": samples * E / (total_ms / 1e3),
+           "view_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "views": int(lat.size)},
+           "frame_latency_ms_amortised": {"p50": float(np.percentile(lat, 50)) / E,
+                                          "p99": float(np.percentile(lat, 99)) / E},
+           "graph": "one CUDA graph per batch (one rt_render_frame_multi per view)",
+           "launch_shape": {"lights_per_launch": shape[0], "warpgroups": shape[1], "tuned_ms": tuned_ms},
+           "gpu_launches": steps * V * max(1, E // shape[0]), "clocks": clk}
+    del srv, gbs, envs
+    r.close()
+    return out
+
+
+def run_serve(args):
+    """Batched serving as its own bench line (--mode serve)."""
+    import torch
+    rank, local, world = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    res = time_serve(args.views, args.lights, args.steps, args.warmup, rank, local)
     if rank != 0:
         return
     line = {"metric": "batched serving: secondary samples/s and frame latency (16 views x 8 env maps, 1920x1080)",
-            "value": samples / (total_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_batch"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"serve1080: {V} views x {E} env maps, 1920x1080, N=256, M=8, L=16, T=2^20, bf16",
-                       "graph": "one CUDA graph per batch (one rt_render_frame_multi per view)",
-                       "launch_shape": {"lights_per_launch": shape[0], "warpgroups": shape[1], "tuned_ms": tuned_ms}},
-            "frames_per_s": frames / (total_ms / 1e3), "lit_samples_per_s": samples * E / (total_ms / 1e3),
-            "view_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                "views": int(lat.size)},
-            "frame_latency_ms_amortised": {"p50": float(np.percentile(lat, 50)) / E,
-                                           "p99": float(np.percentile(lat, 99)) / E},
-            "gpu_launches": args.steps * V * max(1, E // shape[0]), "clocks": clk}
+            "config": {"workload": res["workload"], "graph": res["graph"], "launch_shape": res["launch_shape"]},
+            "frames_per_s": res["frames_per_s"], "lit_samples_per_s": res["lit_samples_per_s"],
+            "view_latency_ms": res["view_latency_ms"], "frame_latency_ms_amortised": res["frame_latency_ms_amortised"],
+            "gpu_launches": res["gpu_launches"], "clocks": res["clocks"]}
     print(json.dumps(line))
 
 
@@ -629,6 +858,10 @@ def main():
                     help="visibility of the main frame leg (the headline is soft)")
     ap.add_argument("--sampling", choices=["cosine", "mis"], default="cosine",
                     help="primary directions of the main frame leg (the headline is cosine)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched-serving leg")
+    ap.add_argument("--serve-steps", type=int, default=2, help="timed batches of the serving leg")
+    ap.add_argument("--no-grad-check", action="store_true",
+                    help="skip the backward's FP64 gradient check (part of the cpu_baseline leg)")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)
     ap.add_argument("--pixels", type=int, default=0,

@@ -287,9 +287,15 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
  * rewritten in full by every call, so it needs no clearing.
  *  - precision must be RT_FP32 (else RT_ERR_UNSUPPORTED); L*F must fit the
  *    array's 32 feature rows (else RT_ERR_INVALID_ARG; every valid config does);
+ *  - sampling = RT_SAMPLE_MIS returns RT_ERR_UNSUPPORTED: MIS draws from the
+ *    texel CDFs of a bound map, which live in a context's workspace;
+ *  - hard visibility (RT_VIS_HARD) and any pixel_offset >= 0 are accepted, as
+ *    in rt_render_frame's FP32 path;
  *  - the first call on a device finds the array's device address
  *    (cudaGetSymbolAddress) and sets the kernel's shared-memory limit, with
- *    that device current; make that first call before any stream capture;
+ *    that device current; make that first call before any stream capture.
+ *    Later calls look the address up again and redo that set-up if it moved
+ *    (the device's context was reset in between);
  *  - all calls on a device share the array: calls whose work overlaps on the
  *    GPU (different streams, or different models in flight) race; serialise
  *    them on one stream;
@@ -298,6 +304,45 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
 rt_status rt_render_frame_static(const rt_config* cfg, const void* table, const float* brdf_w, const float* irt_w,
                                  const float* env, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                                  float* radiance, void* stream);
+
+/* ---- fault-path self-tests ------------------------------------------------
+ * The paper has no counterpart: these two calls let a test drive the
+ * library's own failure handling without faulting or hanging a GPU. */
+
+/* Run the device-side timeout path of the tensor-core kernels: one warp
+ * waits, with their bounded mbarrier wait but a limit of limit_ns (clamped
+ * to 1 ms .. 2 s), on an mbarrier that nothing arrives on, then records a
+ * timeout in ctx's status word and returns; the context stays usable.  The
+ * following rt_check returns RT_ERR_TIMEOUT with word = (1 << 28) | 0xF.
+ * Needs a context (rt_set_params not required); asynchronous on `stream`. */
+rt_status rt_selftest_wait(rt_ctx* ctx, int64_t limit_ns, void* stream);
+
+/* Host-side fault injection for rt_create: the n-th device allocation that
+ * rt_create makes from now on fails as if cudaMalloc had reported an
+ * out-of-memory error (n >= 1; n = 0 disarms; n < 0 is RT_ERR_INVALID_ARG).
+ * It fires once.  rt_create then frees what it had allocated and returns
+ * RT_ERR_OOM with *out left NULL.  Process-wide: not for concurrent use. */
+rt_status rt_debug_fail_alloc(int32_t n);
+
+/* ---- roofline probes (measurement) ----------------------------------------
+ * The paper has no counterpart: these kernels measure the two ceilings the
+ * renderer's kernels are reported against that a stream copy and a library
+ * GEMM do not give.  Time them with events on `stream`; they read nothing
+ * but their arguments and write only `sink`. */
+
+/* Random gathers from an L2-resident table: blocks x 512 threads, each
+ * issuing iters x 8 independent loads of bytes_per_load (4 or 8) bytes at
+ * rows hash(thread, k) mod rows of `table` (device, rows entries of
+ * bytes_per_load bytes; rows a power of two <= 2^31; aligned to
+ * bytes_per_load).  sink [blocks * 512] uint32 (device).  Loads per launch:
+ * blocks * 512 * iters * 8, each one 32-byte L2 sector request. */
+rt_status rt_probe_gather(const void* table, int64_t rows, int32_t bytes_per_load, int32_t iters, int32_t blocks,
+                          uint32_t* sink, void* stream);
+
+/* FP32 FMA throughput: blocks x 512 threads, each running 8 independent
+ * chains of iters x 16 fmaf.  FLOP per launch: blocks * 512 * iters * 256.
+ * sink [blocks * 512] float (device). */
+rt_status rt_probe_ffma(int32_t iters, int32_t blocks, float* sink, void* stream);
 
 /* ---- per-head distillation (Sec. 3.3, supplementary "Training Details") -- */
 

@@ -30,7 +30,8 @@ EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
            "rt_render_frame", "rt_backward", "rt_render_frame_static", "rt_render_frame_multi", "rt_tune",
            "rt_tuned_shape", "rt_set_launch_shape", "rt_denoise", "rt_distill_dirs",
-           "rt_distill_backward", "rt_adam_step"]
+           "rt_distill_backward", "rt_adam_step", "rt_selftest_wait", "rt_debug_fail_alloc",
+           "rt_probe_gather", "rt_probe_ffma"]
 
 
 class RtConfig(ctypes.Structure):
@@ -89,6 +90,10 @@ def _load() -> ctypes.CDLL:
         "rt_distill_dirs": (I32, [P, I64, I32, I64, P, P]),
         "rt_distill_backward": (I32, [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P]),
         "rt_adam_step": (I32, [P, P, P, P, I64, F32, F32, F32, F32, F32, I32, P]),
+        "rt_selftest_wait": (I32, [P, I64, P]),
+        "rt_debug_fail_alloc": (I32, [I32]),
+        "rt_probe_gather": (I32, [P, I64, I32, I32, I32, P, P]),
+        "rt_probe_ffma": (I32, [I32, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +179,23 @@ def adam_step(param: torch.Tensor, grad: torch.Tensor, m1: torch.Tensor, m2: tor
     """rt_adam_step in place on float32 device tensors of equal size."""
     _check("rt_adam_step", LIB.rt_adam_step(_ptr(param), _ptr(grad), _ptr(m1), _ptr(m2), param.numel(), lr, beta1,
                                             beta2, eps, weight_decay, step, _stream()))
+
+
+def probe_gather(table: torch.Tensor, bytes_per_load: int, iters: int, blocks: int,
+                 sink: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """rt_probe_gather over a contiguous device table (its bytes / bytes_per_load rows)."""
+    rows = table.numel() * table.element_size() // bytes_per_load
+    sink = torch.empty(blocks * 512, dtype=torch.int32, device=table.device) if sink is None else sink
+    _check("rt_probe_gather", LIB.rt_probe_gather(_ptr(table), rows, bytes_per_load, iters, blocks, _ptr(sink),
+                                                  _stream()))
+    return sink
+
+
+def probe_ffma(iters: int, blocks: int, sink: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """rt_probe_ffma; returns the sink [blocks * 512] float."""
+    sink = torch.empty(blocks * 512, dtype=torch.float32, device="cuda") if sink is None else sink
+    _check("rt_probe_ffma", LIB.rt_probe_ffma(iters, blocks, _ptr(sink), _stream()))
+    return sink
 
 
 def gbuffer(gb: Dict[str, torch.Tensor]) -> RtGbuffer:

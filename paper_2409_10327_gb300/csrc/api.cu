@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <atomic>
 #include <new>
 
 #include "rt_internal.h"
@@ -94,6 +95,23 @@ ModelDesc model_desc(const rt_ctx* ctx) {
 }
 
 rt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RT_OK : RT_ERR_CUDA; }
+
+// Host-side fault injection (rt_debug_fail_alloc): the number of workspace
+// allocations still to go before one fails; 0 = armed for none.
+std::atomic<int> g_fail_alloc{0};
+
+// cudaMalloc of rt_create's workspace, failing on request as if the device
+// were out of memory.
+cudaError_t ws_malloc(void** p, size_t bytes) {
+  int n = g_fail_alloc.load();
+  while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
 
 rt_status check_ctx(const rt_ctx* ctx) {
   if (ctx == nullptr) return RT_ERR_INVALID_ARG;
@@ -214,22 +232,22 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
     delete ctx;
     return RT_ERR_CUDA;
   }
-  if (cudaMalloc(&ctx->wpack, (size_t)WPACK_FLOATS * 4) != cudaSuccess) {
+  if (ws_malloc((void**)&ctx->wpack, (size_t)WPACK_FLOATS * 4) != cudaSuccess) {
     delete ctx;
     return RT_ERR_OOM;
   }
-  if (cudaMalloc(&ctx->wbf16, (size_t)WBF16_BYTES) != cudaSuccess) {
+  if (ws_malloc((void**)&ctx->wbf16, (size_t)WBF16_BYTES) != cudaSuccess) {
     cudaFree(ctx->wpack);
     delete ctx;
     return RT_ERR_OOM;
   }
-  if (cudaMalloc(&ctx->status, 256) != cudaSuccess || cudaMemset(ctx->status, 0, 256) != cudaSuccess) {
+  if (ws_malloc((void**)&ctx->status, 256) != cudaSuccess || cudaMemset(ctx->status, 0, 256) != cudaSuccess) {
     cudaFree(ctx->wpack);
     cudaFree(ctx->wbf16);
     delete ctx;
     return RT_ERR_OOM;
   }
-  if (cudaMalloc(&ctx->cdf, (size_t)cdf_words(*cfg) * 4) != cudaSuccess) {
+  if (ws_malloc((void**)&ctx->cdf, (size_t)cdf_words(*cfg) * 4) != cudaSuccess) {
     cudaFree(ctx->wpack);
     cudaFree(ctx->wbf16);
     cudaFree(ctx->status);
@@ -295,6 +313,18 @@ rt_status rt_set_params(rt_ctx* ctx, const void* table, const float* brdf_w, con
   h.ib3[1] = host[OFF_IB3 + 1];
   for (int o = 0; o < 8; ++o) h.bb3[o] = host[OFF_BB3 + o];
   ctx->ready = true;
+  return RT_OK;
+}
+
+rt_status rt_selftest_wait(rt_ctx* ctx, int64_t limit_ns, void* stream) {
+  if (ctx == nullptr) return RT_ERR_INVALID_ARG;
+  const int64_t lim = limit_ns < 1000000 ? 1000000 : (limit_ns > 2000000000 ? 2000000000 : limit_ns);
+  return cuda_status(launch_wait_never(ctx->status, (uint64_t)lim, (cudaStream_t)stream));
+}
+
+rt_status rt_debug_fail_alloc(int32_t n) {
+  if (n < 0) return RT_ERR_INVALID_ARG;
+  g_fail_alloc.store(n);
   return RT_OK;
 }
 

@@ -68,6 +68,35 @@ __device__ __forceinline__ void grid_cell(float x, int res, uint32_t& i0, float&
   w = __fsub_rn(g, (float)i);   // exact
 }
 
+// The same cell (decided from the float32 u and g above, so indices stay
+// reproducible) with the fraction taken from the exact grid coordinate: u =
+// x/2 + 1/2 and g = u N are carried as float32 values plus their rounding
+// residuals (Fast2Sum for the sum, an FMA for the product), so w = g - i0 is
+// accurate to the rounding of w itself instead of to the rounding of g
+// (N 2^-24 of a cell, about 1.2e-4 on a 2048 level).  Where the float32 g
+// rounded across a cell face, w lies that hair outside [0, 1]; the trilinear
+// interpolant is continuous across the face, so the feature is unaffected.
+__device__ __forceinline__ void grid_cell_exact(float x, int res, uint32_t& i0, float& w) {
+  const float h = __fmul_rn(x, 0.5f);                       // exact
+  float u = __fadd_rn(h, 0.5f);
+  float ul = __fadd_rn(__fsub_rn(0.5f, u), h);              // u + ul = h + 1/2 exactly when |h| <= 1/2
+  if (u > 1.0f || (u == 1.0f && ul >= 0.0f)) {              // clamp the exact value to [0, 1]
+    u = 1.0f;
+    ul = 0.0f;
+  }
+  if (u < 0.0f || (u == 0.0f && ul <= 0.0f)) {
+    u = 0.0f;
+    ul = 0.0f;
+  }
+  const float rf = (float)res;
+  const float g = __fmul_rn(u, rf);                         // the float32 g of grid_cell
+  int i = (int)floorf(g);
+  i = min(i, res - 1);
+  i0 = (uint32_t)i;
+  const float g_lo = __fmaf_rn(ul, rf, __fmaf_rn(u, rf, -g));   // (u + ul) N - g
+  w = __fadd_rn(__fsub_rn(g, (float)i), g_lo);
+}
+
 __device__ __forceinline__ uint32_t corner_row(uint32_t ix, uint32_t iy, uint32_t iz, int res, int dense,
                                                uint32_t mask) {
   if (dense) {
@@ -93,6 +122,28 @@ __device__ __forceinline__ float2 encode_level(const GridDesc& g, int l, f3 x) {
   grid_cell(x.x, res, ix, wx);
   grid_cell(x.y, res, iy, wy);
   grid_cell(x.z, res, iz, wz);
+  const size_t base = (size_t)l << g.log2T;
+  const int dense = g.dense[l];
+  float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const uint32_t row = corner_row(ix + (c & 1), iy + ((c >> 1) & 1), iz + ((c >> 2) & 1), res, dense, g.mask);
+    const float w = ((c & 1) ? wx : 1.0f - wx) * ((c & 2) ? wy : 1.0f - wy) * ((c & 4) ? wz : 1.0f - wz);
+    const float2 v = table_entry(g, base + row);
+    f0 = fmaf(w, v.x, f0);
+    f1 = fmaf(w, v.y, f1);
+  }
+  return make_float2(f0, f1);
+}
+
+// encode_level with the exact fractions of grid_cell_exact (the FP32 fused kernels).
+__device__ __forceinline__ float2 encode_level_exact(const GridDesc& g, int l, f3 x) {
+  const int res = g.res[l];
+  uint32_t ix, iy, iz;
+  float wx, wy, wz;
+  grid_cell_exact(x.x, res, ix, wx);
+  grid_cell_exact(x.y, res, iy, wy);
+  grid_cell_exact(x.z, res, iz, wz);
   const size_t base = (size_t)l << g.log2T;
   const int dense = g.dense[l];
   float f0 = 0.0f, f1 = 0.0f;

@@ -57,9 +57,9 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
         const int res = m.grid.res[l];
         uint32_t ix, iy, iz;
         float wx, wy, wz;
-        grid_cell(x.x, res, ix, wx);
-        grid_cell(x.y, res, iy, wy);
-        grid_cell(x.z, res, iz, wz);
+        grid_cell_exact(x.x, res, ix, wx);
+        grid_cell_exact(x.y, res, iy, wy);
+        grid_cell_exact(x.z, res, iz, wz);
         const size_t base = (size_t)l << m.grid.log2T;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
@@ -118,7 +118,7 @@ render_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, fl
       const f3 x2 = x + wi * t;
       __syncwarp();
       for (int l = 0; l < m.grid.levels; ++l) {
-        const float2 f = encode_level(m.grid, l, x2);
+        const float2 f = encode_level_exact(m.grid, l, x2);
         actA[aidx(2 * l, lane)] = f.x;
         actA[aidx(2 * l + 1, lane)] = f.y;
       }

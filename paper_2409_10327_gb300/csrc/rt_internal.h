@@ -47,6 +47,10 @@ static_assert(OFF_BW1 % 4 == 0 && OFF_BW3 % 4 == 0 && WPACK_FLOATS % 4 == 0, "fl
 // the 32-byte swizzle, 32-byte rows, 8-row groups 256 bytes apart; a row's
 // sum does not depend on how the swizzle permutes its two 16-byte halves).
 // I layer 1 takes [f (32, zero beyond L*F) | PE (27) | 1 | 1 | 0 (3)].
+// The primary evaluation of I runs in split precision: each operand is the
+// sum of a bf16 hi part and a bf16 lo part (the rounding residual), and the
+// product is hi.hi + lo.hi + hi.lo; the last two tiles hold the lo parts of
+// I's layer-1 and layer-2 weights (zero in the bias columns).
 constexpr int OFFB_IW1 = 0;        // 64 x 64
 constexpr int OFFB_IW2 = 8192;     // 64 x 64
 constexpr int OFFB_BW1 = 16384;    // 64 x 64 (k < L*F, and the bias columns)
@@ -54,7 +58,9 @@ constexpr int OFFB_BW2 = 24576;    // 64 x 64
 constexpr int OFFB_IB2 = 32768;    // 64 x 16, 32-byte swizzle
 constexpr int OFFB_BB2 = 34816;    // 64 x 16, 32-byte swizzle
 constexpr int OFFB_ONES = 36864;   // 128 x 16 of 1.0, 32-byte swizzle
-constexpr int WBF16_BYTES = 40960;
+constexpr int OFFB_IW1L = 40960;   // 64 x 64, lo parts of I's layer 1 (f and PE columns)
+constexpr int OFFB_IW2L = 49152;   // 64 x 64, lo parts of I's layer 2
+constexpr int WBF16_BYTES = 57344;
 constexpr int kBiasCol = 59;       // A-tile / layer-1 columns carrying b1 (hi at 59, lo at 60)
 
 __host__ __device__ constexpr int swz128(int n, int k) {
@@ -131,6 +137,8 @@ cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, 
                                       int max_nl, int wg, cudaStream_t s);
 // Status-word codes: (kStatusTimeout | where) after a bounded wait gave up.
 constexpr uint32_t kStatusTimeout = 1u << 28;
+constexpr uint32_t kWhereSelftest = 0xFu;   // the wait of rt_selftest_wait
+cudaError_t launch_wait_never(uint32_t* status, uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_render_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                float4* out, int num_sms, cudaStream_t s);
 cudaError_t prepare_distill();

@@ -36,16 +36,21 @@ DeviceSlot g_slots[kMaxDevices];
 
 // Once per device, with that device current: the array's device address (the
 // host-side symbol is not a device address), the SM count and the kernel's
-// shared-memory attribute.
+// shared-memory attribute.  Every call looks the address up again (a host-side
+// lookup that allocates nothing): if the device's context was reset since the
+// set-up (cudaDeviceReset), the array lives at a new address in the new
+// context and the kernel attribute is gone, so the set-up is redone instead of
+// launching through a stale pointer.
 rt_status device_slot(DeviceSlot** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return RT_ERR_CUDA;
   if (dev >= kMaxDevices) return RT_ERR_UNSUPPORTED;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_wpack) != cudaSuccess || p == nullptr) return RT_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceSlot& s = g_slots[dev];
-  if (!s.ready) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_wpack) != cudaSuccess || p == nullptr) return RT_ERR_CUDA;
+  if (!s.ready || s.wpack != static_cast<float*>(p)) {
+    s.ready = false;
     if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RT_ERR_CUDA;
     if (prepare_render_fp32() != cudaSuccess) return RT_ERR_CUDA;
     s.wpack = static_cast<float*>(p);

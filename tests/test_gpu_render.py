@@ -106,12 +106,15 @@ def test_empty_frame_and_errors(lib):
     assert r.check() == 0
 
 
-def test_full_size_frame_sampled_against_oracle(lib):
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_full_size_frame_sampled_against_oracle(lib, seed):
     # the 800x800, N=128, M=8, L=16, T=2^19 workload in the bench's launch
-    # configuration, checked on a seeded sample of its pixels
+    # configuration (each of its four timed scenes), checked on 512 seeded pixels
     cfg = scenegen.CONFIGS["frame800"]
-    sc, gb = helpers.scene_arrays(cfg, 0)
+    sc, gb = helpers.scene_arrays(cfg, seed)
     out = _render(cfg, sc, gb)
-    rows = scenegen.subset_permutation(cfg.n_pixels, 48, seed=0)
+    rows = scenegen.subset_permutation(cfg.n_pixels, 512, seed=seed)
     assert np.isfinite(out).all()
-    _parity(cfg, sc, gb, out, rows=rows)
+    stats = _parity(cfg, sc, gb, out, rows=rows)
+    # cosine sampling: the plain frame-wise 1e-4, without the conditioning allowance
+    assert stats["frame_rel_l1"] <= helpers.FP32_FRAME_TOL, stats

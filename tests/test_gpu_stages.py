@@ -31,12 +31,31 @@ def _points(P, seed):
     return pos
 
 
+def _full_points(P, seed):
+    pos = _points(P, seed)
+    rng = np.random.default_rng(seed + 100)
+    # exact vertices of the finest (2048) lattice and points a float32 ulp either side of them
+    v = (2.0 * rng.integers(0, 2049, (256, 3)) / 2048 - 1.0).astype(np.float32)
+    pos[136:392, :3] = v
+    pos[392:648, :3] = np.nextafter(v, np.float32(2.0))
+    pos[648:904, :3] = np.nextafter(v, np.float32(-2.0))
+    return pos
+
+
+@pytest.mark.parametrize("workload", ["small", "frame800", "serve1080"])
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_encode_indices_bit_exact(lib, precision):
-    cfg = helpers.small_cfg(precision=precision)
+def test_encode_indices_bit_exact(lib, precision, workload):
+    # small: L=8, T=2^14, 16..256; frame800: L=16, T=2^19, 16..2048 (the benchmarked grid);
+    # serve1080: L=16, T=2^20, 16..2048 (the batched-serving grid)
+    if workload == "small":
+        cfg = helpers.small_cfg(precision=precision)
+        pos = _points(3001, 1)
+    else:
+        import dataclasses
+        cfg = dataclasses.replace(scenegen.CONFIGS[workload], precision=precision)
+        pos = _full_points(20001, 2)
     sc = scenegen.make_scene(cfg, 0)
     r = helpers.renderer_for(cfg, sc)
-    pos = _points(3001, 1)
     feat, idx, w = r.encode(torch.from_numpy(pos).cuda(), want_aux=True)
     res = hashgrid.level_resolutions(cfg.levels, cfg.base_res, cfg.max_res)
     dense = hashgrid.dense_levels(res, 1 << cfg.log2_T)
