@@ -142,7 +142,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       const int l = lane >> 1;
       float2 part = make_float2(0.f, 0.f);
       if (l < m.grid.levels) {
-        const float2 f = encode_level(m.grid, l, x);
+        const float2 f = encode_level_exact(m.grid, l, x);
         part = (lane & 1) ? make_float2(0.f, 0.f) : f;
       }
       if ((lane & 1) == 0) {
@@ -190,7 +190,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       // ---- f' = H(x') into F2, then B(f')
       __syncwarp();
       for (int l = 0; l < m.grid.levels; ++l) {
-        const float2 f = encode_level(m.grid, l, x2);
+        const float2 f = encode_level_exact(m.grid, l, x2);
         F2[aidx(2 * l, lane)] = f.x;
         F2[aidx(2 * l + 1, lane)] = f.y;
       }
@@ -322,6 +322,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
 
       // ---- encode adjoint at x': table gradients and dLoss/dx'
       f3 dx2 = mk(0.f, 0.f, 0.f);
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
       if (valid) {
         for (int l = 0; l < m.grid.levels; ++l) {
           float d0 = 0.f, d1 = 0.f;
@@ -331,7 +332,7 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
               d0 = dF2[2 * k];
               d1 = dF2[2 * k + 1];
             }
-          encode_level_bwd(m.grid, l, x2, d0, d1, g_table, &dx2);
+          encode_level_bwd_warp(m.grid, l, x2, d0, d1, g_table, &dx2, act);
         }
       }
       const float dt = dot(dx2, wi);

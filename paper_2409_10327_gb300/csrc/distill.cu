@@ -112,7 +112,7 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
         const int l = lane >> 1;
         float2 part = make_float2(0.f, 0.f);
         if (l < levels) {
-          const float2 f = encode_level(m.grid, l, x);
+          const float2 f = encode_level_exact(m.grid, l, x);
           part = (lane & 1) ? make_float2(0.f, 0.f) : f;
         }
         if ((lane & 1) == 0) {
@@ -222,7 +222,7 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
       const f3 x = vp ? xyz(pos4[p]) : mk(0.f, 0.f, 0.f);
 #pragma unroll 1
       for (int l = 0; l < kMaxLevels; ++l) {
-        const float2 f = (vp && l < levels) ? encode_level(m.grid, l, x) : make_float2(0.f, 0.f);
+        const float2 f = (vp && l < levels) ? encode_level_exact(m.grid, l, x) : make_float2(0.f, 0.f);
         F[aidx(2 * l, lane)] = f.x;
         F[aidx(2 * l + 1, lane)] = f.y;
       }
@@ -289,11 +289,12 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
 #pragma unroll
     for (int k = 0; k < 32; ++k) dF[k] = 0.0f;
     bwd_input(H1, sw + OFF_BW1, lf, dF, lane);
+    const unsigned act = __ballot_sync(0xffffffffu, vp);
     if (vp) {
       const f3 x = xyz(pos4[p]);
 #pragma unroll
       for (int l = 0; l < kMaxLevels; ++l)
-        if (l < levels) encode_level_bwd(m.grid, l, x, dF[2 * l], dF[2 * l + 1], g_table, nullptr);
+        if (l < levels) encode_level_bwd_warp(m.grid, l, x, dF[2 * l], dF[2 * l + 1], g_table, nullptr, act);
     }
     __syncwarp();
   }
