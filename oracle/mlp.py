@@ -27,10 +27,13 @@ taken on the logit as a kernel computes it.  'bf16' rounds the layer
 inputs, the two hidden weight matrices and the first hidden activations to
 bfloat16 (round to nearest even) and keeps the biases and the output layer
 in float32, with float64 sums (the tensor cores' float32 accumulation
-differs from them only in summation order); 'fp32' rounds every operand and
-every layer result to float32.  Pins: exact agreement with `mlp3` when all
-roundings are exact, and the rounding of each stage observed on values that
-are not representable (tests/test_oracle_mlp.py).
+differs from them only in summation order); 'bf16x3' is the split form of
+the BF16 kernels' primary evaluation of I: each of those bf16 operands is a
+bf16 hi part plus a bf16 lo part (the rounding residual) and every product
+a.w is taken as a_hi w_hi + a_lo w_hi + a_hi w_lo, dropping only a_lo w_lo;
+'fp32' rounds every operand and every layer result to float32.  Pins: exact
+agreement with `mlp3` when all roundings are exact, and the rounding of each
+stage observed on values that are not representable (tests/test_oracle_mlp.py).
 """
 from __future__ import annotations
 
@@ -79,13 +82,24 @@ def round_to(x: torch.Tensor, arith: str) -> torch.Tensor:
 
 
 def mlp3_arith(z: torch.Tensor, layers: Layers, arith: str) -> torch.Tensor:
-    """mlp3 in a kernel's arithmetic ('bf16' or 'fp32'; see the module notes)."""
+    """mlp3 in a kernel's arithmetic ('bf16', 'bf16x3' or 'fp32'; see the module notes)."""
     (w1, b1), (w2, b2), (w3, b3) = layers
     if arith == "bf16":
         r16 = lambda a: round_to(a, "bf16")
         r32 = lambda a: round_to(a, "fp32")
         h1 = r32(torch.relu(r16(z) @ r16(w1).T + r32(b1)))
         h2 = r32(torch.relu(r16(h1) @ r16(w2).T + r32(b2)))
+        return r32(h2 @ r32(w3).T + r32(b3))
+    if arith == "bf16x3":
+        r16 = lambda a: round_to(a, "bf16")
+        r32 = lambda a: round_to(a, "fp32")
+
+        def mm(a, w):
+            ah, wh = r16(a), r16(w)
+            al, wl = r16(a - ah), r16(w - wh)
+            return ah @ wh.T + al @ wh.T + ah @ wl.T
+        h1 = r32(torch.relu(mm(z, w1) + r32(b1)))
+        h2 = r32(torch.relu(mm(h1, w2) + r32(b2)))
         return r32(h2 @ r32(w3).T + r32(b3))
     if arith == "fp32":
         f = lambda a: a.to(torch.float32)

@@ -181,21 +181,30 @@ def _kernel_logits(x, n, wo, rough, q, prm: Params, opt: Options, res, dense):
 
     The chain that leads to the decisions (f, I, the bounce, f', B, the
     secondary directions, I again) is re-evaluated in opt.decision_arith:
-    the table as the kernel reads it (FP16 for 'bf16'), the cell decision of
-    the hash grid in float32, the features rounded to the MLP input format,
-    and the MLPs in mlp3_arith.  Directions and depth are float64.
+    the table as the kernel reads it (FP16 for 'bf16'), x' rounded to
+    float32, cell fractions as the kernel takes them (from float32 g for the
+    BF16 secondary encode, exact otherwise), the features rounded to the MLP
+    input format,
+    and the MLPs in mlp3_arith (for 'bf16', the primary evaluation of I in
+    the split form 'bf16x3': there the kernel feeds the float32 features).
+    Directions and depth are float64.
     """
     arith = opt.decision_arith
     P, N, M = x.shape[0], opt.n_dirs, opt.m_dirs
     w_i, _, _ = _primary_dirs(x, n, wo, rough, q, prm, opt)                # unjittered, [P, N, 3]
     tab = mlp.round_to(prm.table, "fp16" if arith == "bf16" else "fp32")
     feat = lambda f: mlp.round_to(f, "bf16" if arith == "bf16" else "fp32")
-    f = feat(hashgrid.encode(x, tab, res, dense, fp32_grid=True))
+    # the fused kernels take cell fractions from the exact grid coordinate (float64 here) for the
+    # primary encode, and for the secondary one in FP32; the BF16 secondary encode uses float32 g
+    f32 = mlp.round_to(hashgrid.encode(x, tab, res, dense), "fp32")
+    f = f32 if arith == "bf16" else feat(f32)
     f_rep = f[:, None, :].expand(P, N, f.shape[1]).reshape(P * N, -1)
-    y = mlp.mlp3_arith(torch.cat([f_rep, mlp.positional_encoding(w_i.reshape(P * N, 3))], dim=-1), prm.irt, arith)
+    # the BF16 kernels evaluate I at the primary point in split precision (hi + lo bf16 parts)
+    y = mlp.mlp3_arith(torch.cat([f_rep, mlp.positional_encoding(w_i.reshape(P * N, 3))], dim=-1), prm.irt,
+                       "bf16x3" if arith == "bf16" else arith)
     t = mlp.depth_from_logit(torch.nn.functional.softplus(y[:, 1]), opt.near, opt.far)
     x2 = x[:, None, :] + t.reshape(P, N, 1) * w_i
-    f2 = feat(hashgrid.encode(x2.reshape(P * N, 3), tab, res, dense, fp32_grid=True))
+    f2 = feat(hashgrid.encode(mlp.round_to(x2.reshape(P * N, 3), "fp32"), tab, res, dense, fp32_grid=arith == "bf16"))
     yb = mlp.mlp3_arith(f2, prm.brdf, arith)
     n2 = yb[:, 0:3] / yb[:, 0:3].norm(dim=1, keepdim=True).clamp(min=1e-12)
     slots = 1 + np.arange(M, dtype=np.uint64)

@@ -31,6 +31,7 @@
 
 #include "device_common.cuh"
 #include "fast_math.cuh"
+#include "mbarrier.cuh"
 #include "mis.cuh"
 
 namespace rtk {
@@ -41,23 +42,31 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// I's layer-1 weight of output n and input column k of the A tile [f | PE | 1 | 1 | 0]
+// (the bias columns excluded), from the FP32 image.
+__device__ __forceinline__ float irt_w1(const float* __restrict__ wp, int n, int k) {
+  if (k < 32) return wp[OFF_IW1F + k * 64 + n];
+  if (k < kBiasCol) return wp[OFF_IW1P + (k - 32) * 64 + n];
+  return 0.0f;
+}
+
 // One thread per bf16 element of the image.
 __global__ void repack_bf16_kernel(const float* __restrict__ wp, uint8_t* __restrict__ out) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= WBF16_BYTES / 2) return;
   const int byte = 2 * e;
   __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-  if (byte < OFFB_IB2) {
-    // one of the four 64 x 64 swizzled matrices: invert swz128
-    const int tile = byte / 8192, o = byte % 8192;
+  if (byte < OFFB_IB2 || byte >= OFFB_IW1L) {
+    // one of the six 64 x 64 swizzled matrices: invert swz128
+    const int tile = byte < OFFB_IB2 ? byte / 8192 : 4 + (byte - OFFB_IW1L) / 8192;
+    const int o = byte % 8192;
     const int n = (o / 1024) * 8 + (o % 1024) / 128;
     const int chunk = ((o % 128) / 16) ^ (n & 7);
     const int k = chunk * 8 + (o % 16) / 2;
     float f = 0.0f;
-    if (tile == 0) {                                    // I layer 1: [f | PE | 1 | 1 | 0]
-      if (k < 32) f = wp[OFF_IW1F + k * 64 + n];
-      else if (k < kBiasCol) f = wp[OFF_IW1P + (k - 32) * 64 + n];
-    } else if (tile == 1) {
+    if (tile == 0 || tile == 4) {                       // I layer 1: [f | PE | 1 | 1 | 0]
+      f = irt_w1(wp, n, k);
+    } else if (tile == 1 || tile == 5) {
       f = wp[OFF_IW2 + k * 64 + n];
     } else if (tile == 2) {                             // B layer 1: [f | 0 | b1]
       if (k < 32) f = wp[OFF_BW1 + k * 64 + n];
@@ -65,6 +74,11 @@ __global__ void repack_bf16_kernel(const float* __restrict__ wp, uint8_t* __rest
       f = wp[OFF_BW2 + k * 64 + n];
     }
     v = __float2bfloat16_rn(f);
+    if (tile >= 4) {                                    // the rounding residual of the hi tile
+      __nv_bfloat16 hi, lo;
+      split_bf16(f, hi, lo);
+      v = lo;
+    }
     if (tile == 0 || tile == 2) {
       const float b = tile == 0 ? wp[OFF_IB1 + n] : wp[OFF_BB1 + n];
       __nv_bfloat16 hi, lo;
@@ -108,19 +122,20 @@ constexpr int TM_D = 0, TM_X = 64, TM_H = 96;
 constexpr int kPixSlots = 34;                // pixels touched by one tile when N >= 4
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int SM_W = 0;
-constexpr int WG_FPIX = 0;                   // primary features [34][32] bf16; reused as red[128] float4
-constexpr int WG_MISC = 2560;                // mbarrier (8), then carry[NL] float4 from +16
-constexpr int WG_BYTES = 2816;
+constexpr int WG_FPIX = 0;                   // primary features, bf16 hi parts [34][32]; reused as red[128] float4
+constexpr int WG_FPIX_LO = kPixSlots * 64;   // their bf16 lo parts [34][32]
+constexpr int WG_MISC = 2 * kPixSlots * 64;  // mbarrier (8), then carry[NL] float4 from +16
+constexpr int WG_BYTES = WG_MISC + 256;
 // hard visibility: a ring of 256 queued shadow rows, the row keys of a tile and per-warp counts
-constexpr int WG_QA = 2816;                  // float4 (w_i, t) [256]
+constexpr int WG_QA = WG_BYTES;              // float4 (w_i, t) [256]
 constexpr int WG_QB = WG_QA + 256 * 16;      // int2 (pixel, i) [256]
 constexpr int WG_KEYS = WG_QB + 256 * 8;     // int [128]
 constexpr int WG_CNT = WG_KEYS + 128 * 4;    // int [4]
-constexpr int WG_BYTES_HARD = 9600;
+constexpr int WG_BYTES_HARD = WG_CNT + 128;
 constexpr int SM_WG = WBF16_BYTES;
 static_assert(WG_MISC + 16 + 8 * 16 <= WG_BYTES, "warpgroup block overflow");
 static_assert(WG_CNT + 16 <= WG_BYTES_HARD, "warpgroup block overflow (hard visibility)");
-static_assert(kPixSlots * 64 <= 2560 && 128 * 16 <= 2560, "pixel slots");
+static_assert(128 * 16 <= 2 * kPixSlots * 64 && WG_MISC % 16 == 0 && WG_BYTES_HARD % 16 == 0, "pixel slots");
 
 template <int WG, bool HARD = false>
 struct Layout {
@@ -138,8 +153,6 @@ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 constexpr uint32_t kIdescN64 = idesc_bf16(128, 64);
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -188,35 +201,6 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(phase)
-      : "memory");
-  return ok;
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: true when the phase completed, false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-  if (mbar_try_wait(bar, phase)) return true;
-  const uint64_t t0 = globaltimer();
-  for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, phase)) return true;
-    if (globaltimer() - t0 > 2000000000ull) return false;
-  }
-}
-
 // Warpgroup barrier (named barrier 1 + wg) that also ORs a flag across the group.
 __device__ __forceinline__ int wg_sync_or(int wg, int v) {
   int r;
@@ -253,6 +237,19 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -266,6 +263,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
+// The two bf16 halves of a packed pair as floats (element 2c in the low half).
+__device__ __forceinline__ float bf16_lo_half(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi_half(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+// The bf16 pair of the rounding residuals (a - bf16(a), b - bf16(b)) of a packed pair hi = bf16x2(a, b).
+__device__ __forceinline__ uint32_t pack_residual(float a, float b, uint32_t hi) {
+  return pack_bf16(a - bf16_lo_half(hi), b - bf16_hi_half(hi));
+}
+
 // D <- X . W1^T (k-steps 0..3 of the layer-1 input in TMEM)
 __device__ __forceinline__ void mma_layer1(uint32_t d, uint32_t x_t, uint32_t w_s) {
 #pragma unroll
@@ -282,6 +287,47 @@ __device__ __forceinline__ void mma_brdf_layer1(uint32_t d, uint32_t x_t, uint32
   mma_bf16_ts(d, x_t, sdesc(w_s), kIdescN64, 0u);
   mma_bf16_ts(d, x_t + 8, sdesc(w_s + 32), kIdescN64, 1u);
   mma_bf16_ts(d, x_t + 24, sdesc(w_s + 96), kIdescN64, 1u);
+}
+
+// The primary evaluation of I in split precision.  Every operand is a bf16
+// hi part plus a bf16 lo part (its rounding residual): A = Ah + Al, W = Wh +
+// Wl, and A W ~ Ah Wh + Al Wh + Ah Wl in FP32, which carries about 16
+// significant bits instead of bf16's 8.  The lo operands take the H columns
+// during layer 1 (and X / H hold the hi / lo parts of the hidden layer during
+// layer 2), so the warpgroup's 128 TMEM columns suffice.
+// Layer 1: D <- Xh W1h + Xl W1h + Xh W1l (the bias rides on Xh's ones columns).
+__device__ __forceinline__ void mma_layer1_split(uint32_t d, uint32_t xh_t, uint32_t xl_t, uint32_t w_s,
+                                                 uint32_t wl_s) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mma_bf16_ts(d, xh_t + 8 * k, sdesc(w_s + 32 * k), kIdescN64, k > 0 ? 1u : 0u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mma_bf16_ts(d, xl_t + 8 * k, sdesc(w_s + 32 * k), kIdescN64, 1u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) mma_bf16_ts(d, xh_t + 8 * k, sdesc(wl_s + 32 * k), kIdescN64, 1u);
+}
+// Layer 2: D <- Hh W2h + Hl W2h + Hh W2l + ones . Bias2
+__device__ __forceinline__ void mma_layer2_split(uint32_t d, uint32_t hh_t, uint32_t hl_t, uint32_t w_s,
+                                                 uint32_t wl_s, uint32_t ones_s, uint32_t bias_s) {
+  mma_layer1_split(d, hh_t, hl_t, w_s, wl_s);
+  mma_bf16(d, sdesc32(ones_s), sdesc32(bias_s), kIdescN64, 1u);
+}
+// Split hidden epilogue: Hh = bf16(relu(D)), Hl = bf16(relu(D) - Hh), 16 columns at a time.
+__device__ __forceinline__ void epilogue_hidden_split(uint32_t d_taddr, uint32_t hh_taddr, uint32_t hl_taddr) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t r[16];
+    tmem_ld16(d_taddr + 16 * q, r);
+    tmem_ld_wait();
+    uint32_t qh[8], ql[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float a = fmaxf(__uint_as_float(r[2 * e]), 0.0f), b = fmaxf(__uint_as_float(r[2 * e + 1]), 0.0f);
+      qh[e] = pack_bf16(a, b);
+      ql[e] = pack_residual(a, b, qh[e]);
+    }
+    tmem_st8(hh_taddr + 8 * q, qh);
+    tmem_st8(hl_taddr + 8 * q, ql);
+  }
 }
 
 // hidden epilogue: H[row] = bf16(relu(D[row][0:64])) (the bias is already in D)
@@ -350,7 +396,8 @@ __device__ __forceinline__ float head_vis(uint32_t taddr, const float* w, float 
 // two x-neighbour corners of a cell share one 8-byte load when their rows
 // form an aligned pair (rows r and r ^ 1: a hashed level with even i, or a
 // dense level with an even row), which removes about a quarter of the
-// gathers.
+// gathers.  (Aligned 16-byte loads, which pair the corners three times in
+// four, measured 5 % slower.)
 __device__ __forceinline__ void encode_point_tmem(const GridDesc& g, f3 x, uint32_t x_taddr) {
 #pragma unroll 1
   for (int it = 0; it < kMaxLevels / 4; ++it) {
@@ -408,6 +455,58 @@ __device__ __forceinline__ void store_pe_tmem(uint32_t x_taddr, f3 w) {
   tmem_st16(x_taddr + 16, q);
 }
 
+// X columns 24..31 (elements 48..63) as B's layer 1 reads them: zero but for
+// the two 1.0 columns that carry its bias.  The split primary evaluation of I
+// leaves the hidden layer's hi parts there, so this is rewritten before B.
+__device__ __forceinline__ void store_bias_cols_tmem(uint32_t x_taddr) {
+  uint32_t q[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int k = 48 + 2 * e;   // elements k, k + 1 of the layer-1 input
+    q[e] = pack_bf16((k == kBiasCol || k == kBiasCol + 1) ? 1.0f : 0.0f,
+                     (k + 1 == kBiasCol || k + 1 == kBiasCol + 1) ? 1.0f : 0.0f);
+  }
+  tmem_st8(x_taddr + 24, q);
+}
+
+// The split layer-1 input of the primary evaluation of I: [f | PE(w) | 1 | 1 | 0]
+// as bf16 hi parts into X (xh_taddr) and lo parts into H (xl_taddr).  f's hi
+// and lo parts come from the tile's feature slots; PE(w) is split here (the
+// ones and zeros have no residual).
+__device__ __forceinline__ void store_primary_split(const uint8_t* fpix, int slot, uint32_t xh_taddr,
+                                                    uint32_t xl_taddr, f3 w) {
+#pragma unroll
+  for (int part = 0; part < 2; ++part) {
+    const uint4* src = reinterpret_cast<const uint4*>(fpix + part * WG_FPIX_LO + slot * 64);
+    uint32_t fr[16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 v = src[c];
+      fr[4 * c] = v.x;
+      fr[4 * c + 1] = v.y;
+      fr[4 * c + 2] = v.z;
+      fr[4 * c + 3] = v.w;
+    }
+    tmem_st16(part ? xl_taddr : xh_taddr, fr);
+  }
+  float pe[32];
+  positional_encoding_fast(w, [&](int k, float v) { pe[k] = v; });
+#pragma unroll
+  for (int k = kPE; k < 32; ++k) pe[k] = (k == kBiasCol - 32 || k == kBiasCol - 31) ? 1.0f : 0.0f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t qh[8], ql[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float a = pe[16 * h + 2 * e], b = pe[16 * h + 2 * e + 1];
+      qh[e] = pack_bf16(a, b);
+      ql[e] = pack_residual(a, b, qh[e]);
+    }
+    tmem_st8(xh_taddr + 16 + 8 * h, qh);
+    tmem_st8(xl_taddr + 16 + 8 * h, ql);
+  }
+}
+
 // (a) f = H(x) of a tile's npix pixels into fpix [npix][32] bf16, 32
 // threads per pixel (two per level, four corners each), four pixels per pass.
 __device__ __forceinline__ void gather_primary_features(const GridDesc& g, const float4* __restrict__ pos4,
@@ -422,9 +521,9 @@ __device__ __forceinline__ void gather_primary_features(const GridDesc& g, const
       const int res = g.res[l];
       uint32_t ix, iy, iz;
       float wx, wy, wz;
-      grid_cell(xs.x, res, ix, wx);
-      grid_cell(xs.y, res, iy, wy);
-      grid_cell(xs.z, res, iz, wz);
+      grid_cell_exact(xs.x, res, ix, wx);   // f feeds the split-precision primary evaluation of I
+      grid_cell_exact(xs.y, res, iy, wy);
+      grid_cell_exact(xs.z, res, iz, wz);
       const size_t base = (size_t)l << g.log2T;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
@@ -439,8 +538,12 @@ __device__ __forceinline__ void gather_primary_features(const GridDesc& g, const
     }
     part.x += __shfl_xor_sync(0xffffffffu, part.x, 1);
     part.y += __shfl_xor_sync(0xffffffffu, part.y, 1);
-    if (slot < npix && (lane & 1) == 0)
-      *reinterpret_cast<uint32_t*>(fpix + slot * 64 + 2 * lane) = pack_bf16(part.x, part.y);
+    if (slot < npix && (lane & 1) == 0) {
+      // hi parts for every use of f, lo parts (rounding residuals) for the split primary evaluation of I
+      const uint32_t hi = pack_bf16(part.x, part.y);
+      *reinterpret_cast<uint32_t*>(fpix + slot * 64 + 2 * lane) = hi;
+      *reinterpret_cast<uint32_t*>(fpix + WG_FPIX_LO + slot * 64 + 2 * lane) = pack_residual(part.x, part.y, hi);
+    }
   }
 }
 
@@ -596,6 +699,7 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
                            : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       // (d) x' = x + t w_i and f' = H(x'); (b) B(f')
       encode_point_tmem(m.grid, x + wi * qw.w, X_w);
+      store_bias_cols_tmem(X_w);
       if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) return false;
       epilogue_hidden(D_w, H_w);
       if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_BW2, W_s + OFFB_ONES, W_s + OFFB_BB2); })) return false;
@@ -664,25 +768,14 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
       // MIS: the direction's Eq. 1 weight relative to cosine sampling rides on fr1
       const f3 fr1 = m.mis ? mis_weighted_brdf(m, xyz(ar), ar.w, n, wo, wi)
                            : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
-      {
-        const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
-        uint32_t fr[16];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint4 v = src[c];
-          fr[4 * c] = v.x;
-          fr[4 * c + 1] = v.y;
-          fr[4 * c + 2] = v.z;
-          fr[4 * c + 3] = v.w;
-        }
-        tmem_st16(X_w, fr);
-      }
-      store_pe_tmem(X_w, wi);
+      store_primary_split(fpix, ps, X_w, H_w, wi);
 
-      // (c) I(f, w_i): the hit test and the depth
-      if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) { ok = false; break; }
-      epilogue_hidden(D_w, H_w);
-      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) {
+      // (c) I(f, w_i) in split precision: the hit test and the depth
+      if (!run_mma([&] { mma_layer1_split(D_t, X_t, H_t, W_s + OFFB_IW1, W_s + OFFB_IW1L); })) { ok = false; break; }
+      epilogue_hidden_split(D_w, X_w, H_w);
+      if (!run_mma([&] {
+            mma_layer2_split(D_t, X_t, H_t, W_s + OFFB_IW2, W_s + OFFB_IW2L, W_s + OFFB_ONES, W_s + OFFB_IB2);
+          })) {
         ok = false;
         break;
       }
@@ -771,25 +864,15 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
                            : brdf_eval_fast(xyz(ar), ar.w, n, wi, wo, m.f0, m.lambert);
       f3 le1 = mk(0.f, 0.f, 0.f);
       if (NL == 1) le1 = env_fetch(envs, tap1);
-      {
-        const uint4* src = reinterpret_cast<const uint4*>(fpix + ps * 64);
-        uint32_t fr[16];
-  #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint4 v = src[c];
-          fr[4 * c] = v.x;
-          fr[4 * c + 1] = v.y;
-          fr[4 * c + 2] = v.z;
-          fr[4 * c + 3] = v.w;
-        }
-        tmem_st16(X_w, fr);
-      }
-      store_pe_tmem(X_w, wi);
+      store_primary_split(fpix, ps, X_w, H_w, wi);
 
-      // (c) I(f, w_i)
-      if (!run_mma([&] { mma_layer1(D_t, X_t, W_s + OFFB_IW1); })) break;
-      epilogue_hidden(D_w, H_w);
-      if (!run_mma([&] { mma_layer2(D_t, H_t, W_s + OFFB_IW2, W_s + OFFB_ONES, W_s + OFFB_IB2); })) break;
+      // (c) I(f, w_i) in split precision: it alone sets t, and so x'
+      if (!run_mma([&] { mma_layer1_split(D_t, X_t, H_t, W_s + OFFB_IW1, W_s + OFFB_IW1L); })) break;
+      epilogue_hidden_split(D_w, X_w, H_w);
+      if (!run_mma([&] {
+            mma_layer2_split(D_t, X_t, H_t, W_s + OFFB_IW2, W_s + OFFB_IW2L, W_s + OFFB_ONES, W_s + OFFB_IB2);
+          }))
+        break;
       float v, tdep;
       {
         float z[2];
@@ -812,6 +895,7 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
 
       // (d) bounce: x' = x + t w_i; f' = H(x') into X columns 0..15
       encode_point_tmem(m.grid, x + wi * tdep, X_w);
+      store_bias_cols_tmem(X_w);
 
       // (b) B(f')
       if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) break;

@@ -81,6 +81,6 @@ def test_largest_level_count_and_table(lib):
             sens = orender.float32_sensitivity(gb, prm, opt, draws=4)
             ok, stats = helpers.fp32_parity(out, ref, sens)
         else:
-            sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=4, mlp=True)
+            sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=helpers.BF16_SENS_DRAWS, mlp=True)
             ok, stats = helpers.bf16_parity(out, ref, sens)
         assert ok and np.isfinite(out).all(), (precision, stats)

@@ -56,7 +56,7 @@ def _bf16_hard_check(cfg, sc, gb, out, offset=0, rows=None, psnr=True):
     ref, allow = orender.render(gb, prm, dataclasses.replace(opt, flip_margin=helpers.HARD_MARGIN_BF16),
                                 pixel_offset=offset, rows=rows)
     sens = orender.float32_sensitivity(gb, prm, opt, pixel_offset=offset, rows=rows, rel=helpers.BF16_JITTER,
-                                       draws=4, mlp=True)
+                                       draws=helpers.BF16_SENS_DRAWS, mlp=True)
     got = out[:, :3] if rows is None else out[rows, :3]
     ok, stats = helpers.bf16_parity(got, ref, sens, extra=allow)
     stats["pixels_with_flip_allowance"] = int((allow > 0).any(-1).sum())

@@ -73,7 +73,7 @@ def _bf16_check(cfg, sc, gb, out, offset=0, rows=None, psnr=True, hard=False):
     margins = dict(mis_margin=helpers.MIS_MARGIN, flip_margin=helpers.HARD_MARGIN_BF16 if hard else 0.0)
     ref, extra = orender.render(gb, prm, dataclasses.replace(opt, **margins), pixel_offset=offset, rows=rows)
     sens = orender.float32_sensitivity(gb, prm, opt, pixel_offset=offset, rows=rows, rel=helpers.BF16_JITTER,
-                                       draws=4, mlp=True)
+                                       draws=helpers.BF16_SENS_DRAWS, mlp=True)
     got = out[:, :3] if rows is None else out[rows, :3]
     ok, stats = helpers.bf16_parity(got, ref, sens, extra=extra)
     assert ok, stats

@@ -33,7 +33,7 @@ def _bf16_check(cfg, sc, gb, out, offset=0, rows=None, psnr_min=PSNR_MIN, **mode
     opt = helpers.oracle_options(cfg, **modes)
     ref = orender.render(gb, prm, opt, pixel_offset=offset, rows=rows)
     sens = orender.float32_sensitivity(gb, prm, opt, pixel_offset=offset, rows=rows, rel=helpers.BF16_JITTER,
-                                       draws=4, mlp=True)
+                                       draws=helpers.BF16_SENS_DRAWS, mlp=True)
     got = out[:, :3] if rows is None else out[rows, :3]
     ok, stats = helpers.bf16_parity(got, ref, sens)
     assert ok, stats
@@ -99,23 +99,29 @@ def test_bf16_small_n_is_rejected(lib):
     assert e.value.status == lib.RT_ERR_UNSUPPORTED
 
 
-def test_bf16_full_size_frame_sampled(lib):
-    # the 800x800, N=128, M=8, L=16, T=2^19 BF16 workload as bench.py launches it
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_bf16_full_size_frame_sampled(lib, seed):
+    # the 800x800, N=128, M=8, L=16, T=2^19 BF16 workload as bench.py launches it (each of its
+    # four timed scenes), on 512 seeded pixels
     cfg = scenegen.CONFIGS["frame800_bf16"]
-    sc, gb = helpers.scene_arrays(cfg, 0)
+    sc, gb = helpers.scene_arrays(cfg, seed)
     out = _render(cfg, sc, gb)
     assert np.isfinite(out).all()
-    rows = scenegen.subset_permutation(cfg.n_pixels, 256, seed=0)
+    rows = scenegen.subset_permutation(cfg.n_pixels, 512, seed=seed)
     stats = _bf16_check(cfg, sc, gb, out, rows=rows, psnr_min=None)
-    # PSNR is defined with the peak of the whole FP64 oracle image; the sample's
-    # MSE estimates the frame's.  The peak comes from tests/golden (written by
-    # make_frame_stats.py from the oracle alone).
-    peak = _golden_stat("frame800_seed0_stats.txt", "peak")
+    # PSNR is defined with the peak of the whole FP64 oracle image; the sample's MSE
+    # estimates the frame's.  The peaks come from tests/golden (written by
+    # make_frame_stats.py from the oracle alone).  The frame maximum is set by rare
+    # back-facing views (NoV clamped to 1e-4); the 99.9th percentile is the robust peak.
+    peak = _golden_stat(f"frame800_seed{seed}_stats.txt", "peak")
+    p999 = _golden_stat(f"frame800_seed{seed}_stats.txt", "p999")
     prm = helpers.oracle_params(sc)
     ref = orender.render(gb, prm, helpers.oracle_options(cfg), rows=rows)
     mse = float(((out[rows, :3] - ref) ** 2).mean())
-    frame_psnr = 10.0 * np.log10(peak * peak / mse)
-    assert frame_psnr >= PSNR_MIN, (frame_psnr, stats)
+    psnr_max = 10.0 * np.log10(peak * peak / mse)
+    psnr_p999 = 10.0 * np.log10(p999 * p999 / mse)
+    assert psnr_max >= PSNR_MIN, (psnr_max, psnr_p999, stats)
+    assert psnr_p999 >= PSNR_MIN, (psnr_max, psnr_p999, stats)
 
 
 def _golden_stat(name, key):

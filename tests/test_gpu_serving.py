@@ -92,7 +92,7 @@ def test_multi_light_bf16_against_oracle(lib):
         prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, envs[e])
         opt = helpers.oracle_options(cfg)
         ref = orender.render(gb, prm, opt)
-        sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=4, mlp=True)
+        sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=helpers.BF16_SENS_DRAWS, mlp=True)
         ok, stats = helpers.bf16_parity(out[e, :, :3], ref, sens)
         assert ok and stats["psnr_db"] >= helpers.BF16_PSNR_MIN, (e, stats)
 
@@ -115,6 +115,6 @@ def test_serve1080_full_size_multi_light_sampled(lib):
         prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, envs[e])
         opt = helpers.oracle_options(cfg)
         ref = orender.render(gb, prm, opt, rows=rows)
-        sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, rel=helpers.BF16_JITTER, draws=4, mlp=True)
+        sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, rel=helpers.BF16_JITTER, draws=helpers.BF16_SENS_DRAWS, mlp=True)
         ok, stats = helpers.bf16_parity(out[e, rows, :3], ref, sens)
         assert ok, (e, r.launch_shape(), stats)

@@ -78,7 +78,7 @@ def _one_path(w1, b1, w2, b2, w3, b3):
     return [(t([[w1]]), t([b1])), (t([[w2]]), t([b2])), (t([[w3]]), t([b3]))]
 
 
-@pytest.mark.parametrize("arith", ["bf16", "fp32"])
+@pytest.mark.parametrize("arith", ["bf16", "bf16x3", "fp32"])
 def test_kernel_arith_is_exact_on_representable_values(arith):
     # one-hot layers with power-of-two weights and bf16-representable inputs: no rounding anywhere
     rng = np.random.default_rng(0)
@@ -107,3 +107,19 @@ def test_bf16_arith_rounds_inputs_hidden_weights_and_activations_only():
     # fp32 rounds 1 + 2^-30 away at every stage
     assert mlp.mlp3_arith(torch.tensor([[1.0 + 2 ** -30]], dtype=torch.float64),
                           _one_path(1, 0, 1, 0, 1, 0), "fp32").item() == 1.0
+
+
+def test_bf16x3_arith_keeps_the_residual_and_drops_only_lo_times_lo():
+    one = torch.tensor([[1.0]], dtype=torch.float64)
+    # an input 1 + 2^-9 is 1 in bf16, but its residual 2^-9 survives the split product
+    z = torch.tensor([[1.0 + 2 ** -9]], dtype=torch.float64)
+    assert mlp.mlp3_arith(z, _one_path(1, 0, 1, 0, 1, 0), "bf16x3").item() == 1.0 + 2 ** -9
+    # (1 + 2^-9)(1 + 2^-9) = 1 + 2^-8 + 2^-18: the split keeps hi.hi + lo.hi + hi.lo = 1 + 2^-8
+    # (the hidden activation 1 + 2^-8 is itself split again for layer 2)
+    assert mlp.mlp3_arith(z, _one_path(1 + 2 ** -9, 0, 1, 0, 1, 0), "bf16x3").item() == 1.0 + 2 ** -8
+    assert mlp.mlp3(z, _one_path(1 + 2 ** -9, 0, 1, 0, 1, 0)).item() == 1.0 + 2 ** -8 + 2 ** -18
+    # a hidden weight's residual survives too: 1 . (1 + 2^-9) = 1 + 2^-9 in layer 2
+    assert mlp.mlp3_arith(one, _one_path(1, 0, 1 + 2 ** -9, 0, 1, 0), "bf16x3").item() == 1.0 + 2 ** -9
+    # two bf16 parts hold about 16 significant bits: 1 + 2^-9 + 2^-17 keeps 1 + 2^-9
+    z = torch.tensor([[1.0 + 2 ** -9 + 2 ** -17]], dtype=torch.float64)
+    assert mlp.mlp3_arith(z, _one_path(1, 0, 1, 0, 1, 0), "bf16x3").item() == 1.0 + 2 ** -9
