@@ -269,7 +269,8 @@ def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
 # reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_frame800.txt")
 KERNEL_SOURCES = {
-    "bf16": ["render_bf16.cu", "fast_math.cuh", "mis.cuh", "mbarrier.cuh", "device_common.cuh", "rt_internal.h"],
+    "bf16": ["render_bf16.cu", "tc_common.cuh", "fast_math.cuh", "mis.cuh", "mbarrier.cuh", "device_common.cuh",
+             "rt_internal.h"],
     "fp32": ["render_fp32.cu", "warp_gemm.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
 }
 
@@ -401,22 +402,24 @@ def backward_flop_per_sample(cfg) -> int:
     return 3 * algorithmic_flop_per_sample(cfg)
 
 
-def time_backward(steps: int, warmup: int, barrier, rays: int = 0):
-    """One distillation step on the 65,536-ray x 64-direction batch (FP32): the student's forward,
+def time_backward(steps: int, warmup: int, barrier, rays: int = 0, precision: str = "fp32"):
+    """One distillation step on the 65,536-ray x 64-direction batch: the student's forward,
     dLoss/dL = (L_s - L_t) / (3 P) against a random-weight teacher of the same architecture
-    (teacher seed 1, student seed 2), and rt_backward into zeroed gradient buffers."""
+    (teacher seed 1, student seed 2), and rt_backward into zeroed gradient buffers.  precision 'bf16'
+    runs the tensor-core forward and adjoint on an FP16 table."""
+    import dataclasses
     import torch
     from paper_2409_10327_gb300 import binding
-    cfg = scenegen.CONFIGS["grad65k"]
+    cfg = dataclasses.replace(scenegen.CONFIGS["grad65k"], precision=precision)
     if rays:
-        import dataclasses
         cfg = dataclasses.replace(cfg, width=rays, height=1)
     gb = {k: torch.from_numpy(v).cuda() for k, v in scenegen.make_gbuffer(cfg.n_pixels, 3).items()}
 
     def renderer(seed):
         sc = scenegen.make_scene(cfg, seed, bias_scale=0.1)
         r = binding.Renderer(binding.make_config(cfg))
-        r.set_params(torch.from_numpy(sc.table).cuda(), torch.from_numpy(sc.brdf_blob).cuda(),
+        table = torch.from_numpy(sc.table).cuda()
+        r.set_params(table.half() if precision == "bf16" else table, torch.from_numpy(sc.brdf_blob).cuda(),
                      torch.from_numpy(sc.irt_blob).cuda(), torch.from_numpy(sc.env).cuda())
         return r, sc
     teacher, _ = renderer(1)
@@ -454,13 +457,19 @@ def time_backward(steps: int, warmup: int, barrier, rays: int = 0):
     flop = backward_flop_per_sample(cfg) * cfg.samples
     teacher.close()
     student.close()
-    return {"workload": f"grad65k: {cfg.n_pixels:,} rays x 64 directions, M=8, L=16, T=2^19, fp32, L2 distillation",
+    if precision == "bf16":
+        # the MLP contractions run on the tensor cores: the measured bf16 GEMM rate (burst)
+        pk = (json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}).get("bf16_tflops")
+        roof = {"bound": "tensor", "peak": pk if pk else 1900.0,
+                "peak_source": "of measured (bf16_tflops, burst)" if pk else "of fallback (1.9 PFLOP/s burst)"}
+    else:
+        roof = {"bound": "alu", "peak": FP32_ALU_PEAK_TFLOPS,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}
+    roof.update({"achieved": flop / avg_s / 1e12, "unit": "TFLOP/s", "frac": flop / avg_s / 1e12 / roof["peak"],
+                 "algorithmic_per_launch": flop, "traffic": None})
+    return {"workload": f"grad65k: {cfg.n_pixels:,} rays x 64 directions, M=8, L=16, T=2^19, {precision}, L2 distillation",
             "ms_per_step": total / steps, "backward_ms": statistics.median(bwd),
-            "value": cfg.samples * steps / (total / 1e3), "unit": UNIT, "steps": steps,
-            "roofline": {"bound": "alu", "achieved": flop / avg_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": flop / avg_s / 1e12 / FP32_ALU_PEAK_TFLOPS,
-                         "algorithmic_per_launch": flop, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz (nominal FFMA rate)"}}
+            "value": cfg.samples * steps / (total / 1e3), "unit": UNIT, "steps": steps, "roofline": roof}
 
 
 def time_distill(steps: int, warmup: int, barrier, rays: int = 2048, K: int = 1024):
@@ -524,16 +533,20 @@ def time_distill(steps: int, warmup: int, barrier, rays: int = 2048, K: int = 10
     return out
 
 
-def backward_gradient_check(n_rays: int = 256) -> dict:
+def backward_gradient_check(n_rays: int = 256, precision: str = "fp32") -> dict:
     """The FP64 oracle's gradient of the L2 distillation loss on the 256-ray check subset of the
     differentiation workload (timed on the host cores: the backward's CPU baseline), against the
-    GPU adjoint's gradient on the same rays: per-tensor ||g - g_ref|| / ||g_ref|| and cosine."""
+    GPU adjoint's gradient on the same rays: per-tensor ||g - g_ref|| / ||g_ref|| and cosine.  For
+    'bf16' both sides use the FP16-rounded table the BF16 context reads."""
+    import dataclasses
     import torch
     from oracle import render as orender
     from paper_2409_10327_gb300 import binding
-    cfg = scenegen.CONFIGS["grad65k"]
+    cfg = dataclasses.replace(scenegen.CONFIGS["grad65k"], precision=precision)
     student = scenegen.make_scene(cfg, 2, bias_scale=0.1)
     teacher = scenegen.make_scene(cfg, 1, bias_scale=0.1)
+    if precision == "bf16":
+        student.table = student.table.astype(np.float16).astype(np.float32)
     full = scenegen.make_gbuffer(cfg.n_pixels, 3)
     rows = np.sort(scenegen.subset_permutation(cfg.n_pixels, n_rays, seed=0))
     gb = {k: np.ascontiguousarray(v[rows]) for k, v in full.items()}
@@ -550,7 +563,8 @@ def backward_gradient_check(n_rays: int = 256) -> dict:
     _, g_table, g_brdf, g_irt = orender.distill_gradient(gb, idx, s_prm, torch.from_numpy(target), opt)
     el = time.perf_counter() - t0
     r = binding.Renderer(binding.make_config(cfg))
-    r.set_params(torch.from_numpy(student.table).cuda(), torch.from_numpy(student.brdf_blob).cuda(),
+    table = torch.from_numpy(student.table).cuda()
+    r.set_params(table.half() if precision == "bf16" else table, torch.from_numpy(student.brdf_blob).cuda(),
                  torch.from_numpy(student.irt_blob).cuda(), torch.from_numpy(student.env).cuda())
     dgb = {k: torch.from_numpy(v).cuda() for k, v in gb.items()}
     g4 = torch.zeros(n_rays, 4, device="cuda")
@@ -575,7 +589,7 @@ def backward_gradient_check(n_rays: int = 256) -> dict:
         if nb > 0:
             stats[k] = {"relnorm": float(np.linalg.norm(a.ravel() - b.ravel()) / nb),
                         "cosine": float(np.dot(a.ravel(), b.ravel()) / max(np.linalg.norm(a) * nb, 1e-300))}
-    return {"rays": n_rays, "reference": "FP64 oracle autograd gradient (directions held fixed)",
+    return {"rays": n_rays, "precision": precision, "reference": "FP64 oracle autograd gradient (directions held fixed)",
             "per_tensor": stats, "max_relnorm": max(v["relnorm"] for v in stats.values()),
             "cpu_baseline": {"value": n_rays * cfg.n_dirs / el, "unit": "ray-direction samples/s", "seconds": el,
                              "kind": "oracle", "sample": f"{n_rays} rays x {cfg.n_dirs} directions (forward + gradient)"}}
@@ -714,6 +728,8 @@ def run_ours(args, cfg):
         r = bwd["roofline"]
         r["peak"], r["frac"] = probes["ffma_tflops"], r["achieved"] / probes["ffma_tflops"]
         r["peak_source"] = "of measured (rt_probe_ffma, burst, same run)"
+        # the BF16 tensor-core adjoint of the same batch
+        bwd["bf16"] = time_backward(max(3, args.steps // 4), args.warmup, barrier, precision="bf16")
     # batched serving (16 views x 8 lights at 1920x1080, one CUDA graph per batch)
     srv = None if args.no_serve else time_serve(args.views, args.lights, args.serve_steps, 1, rank, local)
 
@@ -741,6 +757,8 @@ def run_ours(args, cfg):
                          for prec, fr in frames.items()}}
         if bwd is not None and not args.no_grad_check:
             bwd["gradient_check"] = backward_gradient_check()
+            if "bf16" in bwd:
+                bwd["bf16"]["gradient_check"] = backward_gradient_check(precision="bf16")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_frame": ms_step, "higher_is_better": True,
@@ -878,9 +896,11 @@ def main():
     elif args.mode == "backward":
         import torch
         torch.cuda.set_device(0)
-        line = time_backward(args.steps, args.warmup, torch.cuda.synchronize, rays=args.pixels)
+        line = time_backward(args.steps, args.warmup, torch.cuda.synchronize, rays=args.pixels,
+                             precision=args.precision)
         print(json.dumps({"metric": "backward (distillation step) secondary samples/s", "n_gpus": 1,
-                          "warmup": args.warmup, "dtype": "f32", "data": "synthetic", **line}))
+                          "warmup": args.warmup, "dtype": "bf16" if args.precision == "bf16" else "f32",
+                          "data": "synthetic", **line}))
     elif args.mode == "distill":
         import torch
         torch.cuda.set_device(0)

@@ -266,7 +266,15 @@ rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t wa
  * (lane 3 ignored): ACCUMULATES dLoss/dtable into g_table [L][T][F] float and
  * dLoss/dweights into g_brdf / g_irt (float, blob layouts).  Sampled
  * directions are constants of the estimator.  The caller zeroes the
- * gradient buffers.  RT_VIS_HARD is not differentiable: RT_ERR_UNSUPPORTED. */
+ * gradient buffers.  RT_VIS_HARD is not differentiable: RT_ERR_UNSUPPORTED.
+ * On an RT_FP32 context the adjoint runs in FP32 on the CUDA cores.  On an
+ * RT_BF16 context it differentiates the BF16 render as computed (FP16 table,
+ * the primary evaluation of I in split precision) with tensor-core MMAs: the
+ * forward is recomputed, input gradients dZ W^T and weight gradients dZ^T X
+ * run in bf16 with FP32 accumulation, table and weight gradients are summed
+ * in FP32; n_dirs < 4 gives RT_ERR_UNSUPPORTED, as for the BF16 render.
+ * Table gradients arrive by float reductions whose order across warps
+ * varies, so repeated calls agree to rounding, not bit for bit. */
 rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                       const float* d_radiance, float* g_table, float* g_brdf, float* g_irt,
                       void* stream);

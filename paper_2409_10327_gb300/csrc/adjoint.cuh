@@ -248,6 +248,180 @@ __device__ __forceinline__ void encode_level_bwd_warp(const GridDesc& g, int l, 
   }
 }
 
+// Bitonic sort of one 32-bit key per lane across the warp, ascending with the
+// lane index.  All 32 lanes take part.
+__device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t other = __shfl_xor_sync(0xffffffffu, key, j);
+      const bool up = (lane & (unsigned)k) == 0u;     // this k-block is sorted ascending
+      const bool lower = (lane & (unsigned)j) == 0u;  // this lane is the lower position of its pair
+      key = (lower == up) ? min(key, other) : max(key, other);
+    }
+  }
+  return key;
+}
+// An integer of up to 10 bits spread to every third bit (the Morton interleave of one axis).
+__device__ __forceinline__ uint32_t morton_spread(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+// The cell of coordinate u in [-1, 1] on a 256-cell axis (clamped).
+__device__ __forceinline__ uint32_t morton_cell8(float u) {
+  const float q = fminf(fmaxf((u * 0.5f + 0.5f) * 256.0f, 0.0f), 255.0f);
+  return (uint32_t)q;
+}
+
+// The encode adjoint at the warp's 32 points (one per lane; `valid` marks the
+// real ones): for every level, the table
+// gradient of the 8 corners of each point's cell and dLoss/dx.  df holds the
+// lane's dLoss/df as FP32 bits, features (2l, 2l + 1) of level l.
+// Segmented scatter: the warp's points are first put in Morton order of their
+// position (8 bits per axis) by a bitonic sort across the lanes, so that points
+// that share a table row on a level sit, for the most part, in consecutive
+// lanes.  Each run of consecutive lanes on one row is summed by a shuffle tree
+// bounded by the run (a fixed order of additions) and reaches the table as one
+// float2 reduction; a row whose points are not consecutive receives one
+// reduction per run.  Levels without runs cost one ballot per corner over the
+// plain scatter.  Returns dLoss/dx of this lane's own point; scratch is 512
+// bytes of the warp's shared memory (the points' dx on their way back).
+__device__ __forceinline__ f3 encode_bwd_sorted(const GridDesc& g, f3 x, const uint32_t (&df)[32], bool valid,
+                                                float* __restrict__ g_table, float4* scratch) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint32_t code = (morton_spread(morton_cell8(x.x)) << 2) | (morton_spread(morton_cell8(x.y)) << 1) |
+                        morton_spread(morton_cell8(x.z));   // 24 bits
+  // key: invalid flag, Morton code, lane (unique, so the sort is a permutation of the lanes)
+  const uint32_t key = warp_sort_u32((valid ? 0u : 0x80000000u) | (code << 5) | lane);
+  const int src = (int)(key & 31u);
+  const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+  const bool live = (int)lane < nv;   // the valid points come first in the sorted order
+  const f3 xs = mk(__shfl_sync(0xffffffffu, x.x, src), __shfl_sync(0xffffffffu, x.y, src),
+                   __shfl_sync(0xffffffffu, x.z, src));
+  uint32_t d[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) d[k] = __shfl_sync(0xffffffffu, df[k], src);
+
+  f3 dx = mk(0.f, 0.f, 0.f);
+#pragma unroll 1
+  for (int l = 0; l < g.levels; ++l) {
+    float df0 = 0.f, df1 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k == l) {
+        df0 = __uint_as_float(d[2 * k]);
+        df1 = __uint_as_float(d[2 * k + 1]);
+      }
+    const int res = g.res[l];
+    uint32_t ix, iy, iz;
+    float wx, wy, wz;
+    grid_cell_exact(xs.x, res, ix, wx);
+    grid_cell_exact(xs.y, res, iy, wy);
+    grid_cell_exact(xs.z, res, iz, wz);
+    const size_t base = (size_t)l << g.log2T;
+    const int dense = g.dense[l];
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+      const uint32_t row = corner_row(ix + ox, iy + oy, iz + oz, res, dense, g.mask);
+      const float ax = ox ? wx : 1.0f - wx, ay = oy ? wy : 1.0f - wy, az = oz ? wz : 1.0f - wz;
+      const float w = ax * ay * az;
+      float v0 = w * df0, v1 = w * df1;
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, row, 1);
+      const bool head = lane == 0u || prev != row || !live;
+      const unsigned heads = __ballot_sync(0xffffffffu, head);
+      if (heads != 0xffffffffu) {
+        // this lane's run is [lane, end): end is the next head (32 if none)
+        const unsigned rest = heads & ~((2u << lane) - 1u);
+        const unsigned end = rest ? (unsigned)(__ffs(rest) - 1) : 32u;
+        const unsigned span = __reduce_max_sync(0xffffffffu, head ? end - lane : 0u);
+        for (unsigned s = 1; s < span; s <<= 1) {
+          const float o0 = __shfl_down_sync(0xffffffffu, v0, s);
+          const float o1 = __shfl_down_sync(0xffffffffu, v1, s);
+          if (lane + s < end) {
+            v0 += o0;
+            v1 += o1;
+          }
+        }
+      }
+      if (head && live) atomicAdd(reinterpret_cast<float2*>(g_table) + base + row, make_float2(v0, v1));
+      if (live) {
+        const float2 e = table_entry(g, base + row);
+        const float de = e.x * df0 + e.y * df1;
+        gx += de * (ox ? 1.0f : -1.0f) * ay * az;
+        gy += de * (oy ? 1.0f : -1.0f) * ax * az;
+        gz += de * (oz ? 1.0f : -1.0f) * ax * ay;
+      }
+    }
+    // dg/dx = N_l / 2 inside the box, 0 on a clamped axis
+    const float s = 0.5f * (float)res;
+    const float ux = xs.x * 0.5f + 0.5f, uy = xs.y * 0.5f + 0.5f, uz = xs.z * 0.5f + 0.5f;
+    dx.x += (ux >= 0.0f && ux <= 1.0f) ? gx * s : 0.0f;
+    dx.y += (uy >= 0.0f && uy <= 1.0f) ? gy * s : 0.0f;
+    dx.z += (uz >= 0.0f && uz <= 1.0f) ? gz * s : 0.0f;
+  }
+  // back to the lane that owns the point
+  scratch[src] = make_float4(dx.x, dx.y, dx.z, 0.0f);
+  __syncwarp();
+  const float4 r = scratch[lane];
+  __syncwarp();
+  return mk(r.x, r.y, r.z);
+}
+
+// s = D F Vis of the simplified Disney model and its derivatives with respect
+// to the roughness r and the normal n (w_i, w_o fixed).  The n-derivative is
+// the textbook one (n.h, n.w_i, n.w_o as independent inputs); the component
+// along n is irrelevant because the decoder's normal is normalised.
+__device__ __forceinline__ float spec_with_grad(float rough, f3 n, f3 wi, f3 wo, float f0, float& ds_dr, f3& ds_dn) {
+  const float alpha = rough * rough;
+  const float a2 = alpha * alpha;
+  const float ndl = dot(n, wi), ndv = dot(n, wo);
+  const float nol = fmaxf(ndl, 0.0f), nov = fmaxf(ndv, 1e-4f);
+  const f3 hv = wi + wo;
+  const float hl2 = dot(hv, hv);
+  f3 h = mk(0.f, 0.f, 0.f);
+  float ndh = 0.0f, voh = 0.0f, q = 1.0f;
+  if (hl2 > 1e-20f) {
+    const float inv = rsqrtf(hl2);
+    h = hv * inv;
+    ndh = dot(n, h);
+    voh = 0.5f * hl2 * inv;
+    if (ndh > 0.0f) {
+      const f3 c = cross(n, h);
+      q = dot(c, c) + ndh * ndh * a2;     // = (n.h)^2 (a2 - 1) + 1 on the unit sphere
+    }
+  }
+  const float noh = fmaxf(ndh, 0.0f);
+  const float D = a2 / (kPi * q * q);
+  const float om = 1.0f - voh;
+  const float om2 = om * om;
+  const float F = f0 + (1.0f - f0) * (om2 * om2 * om);
+  const float A = sqrtf(nov * nov * (1.0f - a2) + a2);
+  const float B = sqrtf(nol * nol * (1.0f - a2) + a2);
+  const float den = nol * A + nov * B;
+  const float vis = 0.5f / den;
+  const float dD_da2 = 1.0f / (kPi * q * q) - 2.0f * a2 * noh * noh / (kPi * q * q * q);
+  const float dD_dnoh = -4.0f * a2 * noh * (a2 - 1.0f) / (kPi * q * q * q);
+  const float dvis_dden = -0.5f / (den * den);
+  const float dden_da2 = nol * (1.0f - nov * nov) / (2.0f * A) + nov * (1.0f - nol * nol) / (2.0f * B);
+  const float dden_dnol = A + nov * nol * (1.0f - a2) / B;
+  const float dden_dnov = nol * nov * (1.0f - a2) / A + B;
+  const float ds_da2 = F * (dD_da2 * vis + D * dvis_dden * dden_da2);
+  ds_dr = ds_da2 * 4.0f * rough * rough * rough;
+  const float g_nol = ndl > 0.0f ? F * D * dvis_dden * dden_dnol : 0.0f;
+  const float g_nov = ndv > 1e-4f ? F * D * dvis_dden * dden_dnov : 0.0f;
+  const float g_noh = ndh > 0.0f ? F * vis * dD_dnoh : 0.0f;
+  ds_dn = wi * g_nol + wo * g_nov + h * g_noh;
+  return D * F * vis;
+}
+
 // Add the CTA's accumulated gradients of I into the caller's blob (canonical
 // layout of rt_param_count); called by all threads after a barrier.
 __device__ __forceinline__ void flush_irt_grads(const float* sg, int lf, float* __restrict__ g_irt, int nthreads) {

@@ -526,6 +526,12 @@ rt_status rt_backward(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixe
   if (!check_gbuffer(gb) || !check_plane(d_radiance) || g_table == nullptr || !aligned(g_table, 8) ||
       g_brdf == nullptr || !aligned(g_brdf, 4) || g_irt == nullptr || !aligned(g_irt, 4))
     return RT_ERR_INVALID_ARG;
+  if (ctx->cfg.precision == RT_BF16) {
+    if (ctx->cfg.n_dirs < 4) return RT_ERR_UNSUPPORTED;   // as the BF16 render: a tile spans at most 34 pixels
+    return cuda_status(launch_backward_bf16(model_desc(ctx), ctx->head, *gb, (int)P, pixel_offset,
+                                            reinterpret_cast<const float4*>(d_radiance), g_table, g_brdf, g_irt,
+                                            ctx->num_sms, (cudaStream_t)stream));
+  }
   return cuda_status(launch_backward_fp32(model_desc(ctx), *gb, (int)P, pixel_offset,
                                           reinterpret_cast<const float4*>(d_radiance), g_table, g_brdf, g_irt,
                                           ctx->num_sms, (cudaStream_t)stream));

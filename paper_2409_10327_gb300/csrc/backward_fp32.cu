@@ -51,53 +51,6 @@ static_assert(WB_F2 % 4 == 0 && WB_H1 % 4 == 0 && WB_H2 % 4 == 0 &&
                   WB_DZ % 4 == 0 && WB_FLOATS % 4 == 0 && G_FLOATS % 4 == 0,
               "float4 alignment");
 
-// s = D F Vis of the simplified Disney model and its derivatives with respect
-// to the roughness r and the normal n (w_i, w_o fixed).  The n-derivative is
-// the textbook one (n.h, n.w_i, n.w_o as independent inputs); the component
-// along n is irrelevant because the decoder's normal is normalised.
-__device__ __forceinline__ float spec_with_grad(float rough, f3 n, f3 wi, f3 wo, float f0, float& ds_dr, f3& ds_dn) {
-  const float alpha = rough * rough;
-  const float a2 = alpha * alpha;
-  const float ndl = dot(n, wi), ndv = dot(n, wo);
-  const float nol = fmaxf(ndl, 0.0f), nov = fmaxf(ndv, 1e-4f);
-  const f3 hv = wi + wo;
-  const float hl2 = dot(hv, hv);
-  f3 h = mk(0.f, 0.f, 0.f);
-  float ndh = 0.0f, voh = 0.0f, q = 1.0f;
-  if (hl2 > 1e-20f) {
-    const float inv = rsqrtf(hl2);
-    h = hv * inv;
-    ndh = dot(n, h);
-    voh = 0.5f * hl2 * inv;
-    if (ndh > 0.0f) {
-      const f3 c = cross(n, h);
-      q = dot(c, c) + ndh * ndh * a2;     // = (n.h)^2 (a2 - 1) + 1 on the unit sphere
-    }
-  }
-  const float noh = fmaxf(ndh, 0.0f);
-  const float D = a2 / (kPi * q * q);
-  const float om = 1.0f - voh;
-  const float om2 = om * om;
-  const float F = f0 + (1.0f - f0) * (om2 * om2 * om);
-  const float A = sqrtf(nov * nov * (1.0f - a2) + a2);
-  const float B = sqrtf(nol * nol * (1.0f - a2) + a2);
-  const float den = nol * A + nov * B;
-  const float vis = 0.5f / den;
-  const float dD_da2 = 1.0f / (kPi * q * q) - 2.0f * a2 * noh * noh / (kPi * q * q * q);
-  const float dD_dnoh = -4.0f * a2 * noh * (a2 - 1.0f) / (kPi * q * q * q);
-  const float dvis_dden = -0.5f / (den * den);
-  const float dden_da2 = nol * (1.0f - nov * nov) / (2.0f * A) + nov * (1.0f - nol * nol) / (2.0f * B);
-  const float dden_dnol = A + nov * nol * (1.0f - a2) / B;
-  const float dden_dnov = nol * nov * (1.0f - a2) / A + B;
-  const float ds_da2 = F * (dD_da2 * vis + D * dvis_dden * dden_da2);
-  ds_dr = ds_da2 * 4.0f * rough * rough * rough;
-  const float g_nol = ndl > 0.0f ? F * D * dvis_dden * dden_dnol : 0.0f;
-  const float g_nov = ndv > 1e-4f ? F * D * dvis_dden * dden_dnov : 0.0f;
-  const float g_noh = ndh > 0.0f ? F * vis * dD_dnoh : 0.0f;
-  ds_dn = wi * g_nol + wo * g_nov + h * g_noh;
-  return D * F * vis;
-}
-
 // ---- warp-level pieces of an MLP backward -----------------------------------
 
 __global__ void __launch_bounds__(kBT, 1)

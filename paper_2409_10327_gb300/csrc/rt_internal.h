@@ -158,6 +158,10 @@ inline int guide_shift(int n) {
 }
 cudaError_t launch_denoise(int W, int H, const float4* rad, const float* z, const float4* nrm, int iterations,
                            float sigma_z, float sigma_n, float sigma_l, float4* work, float4* out, cudaStream_t s);
+cudaError_t prepare_backward_bf16();
+cudaError_t launch_backward_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P, long long offset,
+                                 const float4* dL, float* g_table, float* g_brdf, float* g_irt, int num_sms,
+                                 cudaStream_t s);
 cudaError_t launch_backward_fp32(const ModelDesc& m, const rt_gbuffer& gb, int P, long long offset,
                                  const float4* dL, float* g_table, float* g_brdf, float* g_irt, int num_sms,
                                  cudaStream_t s);

@@ -298,6 +298,7 @@ cudaError_t prepare_kernels() {
   cudaError_t e = prepare_render_fp32();
   if (e == cudaSuccess) e = prepare_render_bf16();
   if (e == cudaSuccess) e = prepare_backward_fp32();
+  if (e == cudaSuccess) e = prepare_backward_bf16();
   if (e == cudaSuccess) e = prepare_distill();
   if (e == cudaSuccess) e = cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
   return e;
