@@ -273,21 +273,12 @@ backward_fp32_kernel(ModelDesc m, rt_gbuffer gb, int P, long long pixel_offset, 
       bwd_weights(F2, lf, H1, gB.w1(), lf, 0, gB.b1(), lane);
       bwd_input(H1, sw + OFF_BW1, lf, dF2, lane);
 
-      // ---- encode adjoint at x': table gradients and dLoss/dx'
-      f3 dx2 = mk(0.f, 0.f, 0.f);
-      const unsigned act = __ballot_sync(0xffffffffu, valid);
-      if (valid) {
-        for (int l = 0; l < m.grid.levels; ++l) {
-          float d0 = 0.f, d1 = 0.f;
+      // ---- encode adjoint at x': table gradients (segmented scatter over the warp's points in Morton
+      // order) and dLoss/dx'; H2's buffer, free until the next store_pe, carries dx' back to its lane
+      uint32_t dbits[32];
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (k == l) {
-              d0 = dF2[2 * k];
-              d1 = dF2[2 * k + 1];
-            }
-          encode_level_bwd_warp(m.grid, l, x2, d0, d1, g_table, &dx2, act);
-        }
-      }
+      for (int k = 0; k < 32; ++k) dbits[k] = __float_as_uint(dF2[k]);
+      const f3 dx2 = encode_bwd_sorted(m.grid, x2, dbits, valid, g_table, reinterpret_cast<float4*>(H2));
       const float dt = dot(dx2, wi);
       const float dz1 = (sp <= 1.0f) ? dt * (m.far_t - m.near_t) * sigmoidf_(z.y) : 0.0f;
       const float dz0p = (m.force_vis >= 0.f || !valid) ? 0.0f : dv * v * (1.0f - v);
