@@ -794,8 +794,10 @@ def time_serve(views: int, lights: int, steps: int, warmup: int, rank: int = 0, 
            for v in range(V)]
     envs = torch.from_numpy(np.stack([scenegen.make_env(cfg.env_h, cfg.env_w, 100 + e) for e in range(E)])).cuda()
     srv = serve.BatchedServer(r, gbs, envs)
-    tuned_ms = srv.tune()
+    tune_pixels = cfg.n_pixels // 8            # the search runs on the first eighth of view 0
+    tuned_ms = srv.tune(pixels=tune_pixels)
     shape = r.launch_shape()
+    dpt = r.tile_shape()
     srv.capture()
     for _ in range(warmup):
         srv.replay()
@@ -825,7 +827,8 @@ def time_serve(views: int, lights: int, steps: int, warmup: int, rank: int = 0, 
            "frame_latency_ms_amortised": {"p50": float(np.percentile(lat, 50)) / E,
                                           "p99": float(np.percentile(lat, 99)) / E},
            "graph": "one CUDA graph per batch (one rt_render_frame_multi per view)",
-           "launch_shape": {"lights_per_launch": shape[0], "warpgroups": shape[1], "tuned_ms": tuned_ms},
+           "launch_shape": {"lights_per_launch": shape[0], "warpgroups": shape[1], "dirs_per_tile": dpt,
+                            "tuned_ms": tuned_ms, "tuned_on_pixels": tune_pixels},
            "gpu_launches": steps * V * max(1, E // shape[0]), "clocks": clk}
     del srv, gbs, envs
     r.close()

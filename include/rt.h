@@ -248,11 +248,13 @@ rt_status rt_render_frame(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t 
 rt_status rt_render_frame_multi(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset,
                                 const float* envs, int32_t E, float* radiance, void* stream);
 
-/* Autotuner of rt_render_frame_multi's launch shape: times every shape (lights
- * per launch 1/2/4/8 up to E, warpgroups per CTA 2/3/4) once after a warm-up on
- * this workload, writing radiance as rt_render_frame_multi does, keeps the
- * fastest in the context and returns its time in *best_ms (may be NULL; -1
- * for the FP32 path, which has one shape).  Synchronises `stream`. */
+/* Autotuner of rt_render_frame_multi's launch shape: times every shape (tile
+ * shape 128/64/32 directions per tile, see rt_set_tile_shape; lights per launch
+ * 1/2/4/8 up to E; warpgroups per CTA 2/3/4) once after a warm-up on this
+ * workload, writing radiance as rt_render_frame_multi does, keeps the fastest
+ * in the context and returns its time in *best_ms (may be NULL; -1 for the
+ * FP32 path, which has one shape).  Tile shapes that do not divide n_dirs, or
+ * RT_VIS_HARD, are skipped.  Synchronises `stream`. */
 rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_offset, const float* envs, int32_t E,
                   float* radiance, void* stream, float* best_ms);
 
@@ -261,6 +263,18 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
  * renders ignore the warpgroups part (always 4). */
 rt_status rt_tuned_shape(const rt_ctx* ctx, int32_t* lights_per_launch, int32_t* warpgroups);
 rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t warpgroups);
+
+/* Read or force the BF16 tile shape (soft visibility): dirs_per_tile = 128
+ * walks the samples (pixel, direction) in tiles of 128 consecutive samples;
+ * 64 or 32, with n_dirs a larger multiple of it, makes each 128-row tile
+ * 128 / dirs_per_tile pixels x dirs_per_tile directions, the warpgroup
+ * finishing a pixel group's direction chunks before the next group (Sec. 3.2:
+ * the per-point work over directions).  Every row computes the same values in
+ * either order and, for n_dirs a multiple of 32, the pixel sums are added in
+ * the same order, so the radiance bits do not depend on the shape.  Other
+ * values: RT_ERR_INVALID_ARG.  Default 128; rt_tune may change it. */
+rt_status rt_tuned_tile_shape(const rt_ctx* ctx, int32_t* dirs_per_tile);
+rt_status rt_set_tile_shape(rt_ctx* ctx, int32_t dirs_per_tile);
 
 /* Adjoint of rt_render_frame for an upstream gradient d_radiance [P][4]
  * (lane 3 ignored): ACCUMULATES dLoss/dtable into g_table [L][T][F] float and

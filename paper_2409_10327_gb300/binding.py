@@ -29,7 +29,7 @@ EXPORTS = ["rt_status_str", "rt_config_default", "rt_config_validate", "rt_level
            "rt_level_is_dense", "rt_param_count", "rt_workspace_bytes", "rt_create", "rt_destroy",
            "rt_set_params", "rt_check", "rt_encode", "rt_decode", "rt_trace", "rt_sample", "rt_shade",
            "rt_render_frame", "rt_backward", "rt_render_frame_static", "rt_render_frame_multi", "rt_tune",
-           "rt_tuned_shape", "rt_set_launch_shape", "rt_denoise", "rt_distill_dirs",
+           "rt_tuned_shape", "rt_set_launch_shape", "rt_tuned_tile_shape", "rt_set_tile_shape", "rt_denoise", "rt_distill_dirs",
            "rt_distill_backward", "rt_adam_step", "rt_selftest_wait", "rt_debug_fail_alloc",
            "rt_probe_gather", "rt_probe_ffma"]
 
@@ -86,6 +86,8 @@ def _load() -> ctypes.CDLL:
         "rt_tune": (I32, [P, ctypes.POINTER(RtGbuffer), I64, I64, P, I32, P, P, ctypes.POINTER(ctypes.c_float)]),
         "rt_tuned_shape": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "rt_set_launch_shape": (I32, [P, I32, I32]),
+        "rt_tuned_tile_shape": (I32, [P, ctypes.POINTER(I32)]),
+        "rt_set_tile_shape": (I32, [P, I32]),
         "rt_denoise": (I32, [I32, I32, P, P, P, I32, F32, F32, F32, P, P, P]),
         "rt_distill_dirs": (I32, [P, I64, I32, I64, P, P]),
         "rt_distill_backward": (I32, [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P]),
@@ -312,6 +314,15 @@ class Renderer:
 
     def set_launch_shape(self, lights_per_launch: int, warpgroups: int) -> None:
         _check("rt_set_launch_shape", LIB.rt_set_launch_shape(self.ctx, lights_per_launch, warpgroups))
+
+    def tile_shape(self) -> int:
+        """Directions of a pixel per 128-row tile of the BF16 kernel (128: consecutive samples)."""
+        d = ctypes.c_int32()
+        _check("rt_tuned_tile_shape", LIB.rt_tuned_tile_shape(self.ctx, ctypes.byref(d)))
+        return d.value
+
+    def set_tile_shape(self, dirs_per_tile: int) -> None:
+        _check("rt_set_tile_shape", LIB.rt_set_tile_shape(self.ctx, dirs_per_tile))
 
     def render_frame_host(self, gb_host: Dict[str, torch.Tensor], out_host: torch.Tensor,
                           staging: Dict[str, torch.Tensor], out_dev: torch.Tensor, pixel_offset: int = 0) -> None:

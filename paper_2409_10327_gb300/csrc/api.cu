@@ -27,6 +27,7 @@ struct rt_ctx {
   bool ready;
   int tuned_nl;        // lights per launch of the BF16 kernel (rt_tune), default 8
   int tuned_wg;        // warpgroups per CTA of the BF16 kernel (rt_tune), default 4
+  int tuned_dpt;       // directions of a pixel per 128-row tile of the BF16 kernel (rt_tune), default 128
 };
 
 namespace {
@@ -90,6 +91,7 @@ ModelDesc model_desc(const rt_ctx* ctx) {
   m.gm_shift = guide_shift(c.env_h);
   m.gc_shift = guide_shift(c.env_w);
   m.lambert = c.brdf_mode == RT_LAMBERT;
+  m.dpt = ctx->tuned_dpt;
   m.seed = c.dir_seed;
   return m;
 }
@@ -223,6 +225,7 @@ rt_status rt_create(const rt_config* cfg, rt_ctx** out) {
   ctx->cfg = *cfg;
   ctx->tuned_nl = 8;
   ctx->tuned_wg = 4;
+  ctx->tuned_dpt = 128;
   for (int l = 0; l < cfg->levels; ++l) {
     ctx->res[l] = level_res(cfg, l);
     ctx->dense[l] = level_dense(cfg, ctx->res[l]) ? 1 : 0;
@@ -466,28 +469,35 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
     cudaEventDestroy(e0);
     return RT_ERR_CUDA;
   }
-  const ModelDesc m = model_desc(ctx);
+  ModelDesc m = model_desc(ctx);
   const float4* env4 = reinterpret_cast<const float4*>(envs);
   float4* out4 = reinterpret_cast<float4*>(radiance);
   float best = 3.0e38f;
-  int best_nl = ctx->tuned_nl, best_wg = ctx->tuned_wg;
+  int best_nl = ctx->tuned_nl, best_wg = ctx->tuned_wg, best_dpt = ctx->tuned_dpt;
   st = RT_OK;
-  for (int wg = ctx->cfg.visibility == RT_VIS_HARD ? 4 : 2; wg <= 4 && st == RT_OK; ++wg) {
-    for (int nl = 1; nl <= 8 && st == RT_OK; nl *= 2) {
-      if (nl > 1 && nl / 2 >= E) break;   // wider launches than E lights repeat the previous shape
-      float ms = 0.0f;
-      for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {   // rep 0 warms up
-        if (cudaEventRecord(e0, s) != cudaSuccess ||
-            launch_render_bf16_lights(m, ctx->head, *gb, (int)P, pixel_offset, env4, E, out4, ctx->num_sms, nl, wg,
-                                      s) != cudaSuccess ||
-            cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-          st = RT_ERR_CUDA;
-      }
-      if (st == RT_OK && ms < best) {
-        best = ms;
-        best_nl = nl;
-        best_wg = wg;
+  const int N = ctx->cfg.n_dirs;
+  for (int dpt = 128; dpt >= 32 && st == RT_OK; dpt /= 2) {
+    // a tile of 128 / dpt pixels x dpt directions; other shapes repeat the consecutive order
+    if (dpt < 128 && (ctx->cfg.visibility == RT_VIS_HARD || N % dpt != 0 || N <= dpt)) continue;
+    m.dpt = dpt;
+    for (int wg = ctx->cfg.visibility == RT_VIS_HARD ? 4 : 2; wg <= 4 && st == RT_OK; ++wg) {
+      for (int nl = 1; nl <= 8 && st == RT_OK; nl *= 2) {
+        if (nl > 1 && nl / 2 >= E) break;   // wider launches than E lights repeat the previous shape
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && st == RT_OK; ++rep) {   // rep 0 warms up
+          if (cudaEventRecord(e0, s) != cudaSuccess ||
+              launch_render_bf16_lights(m, ctx->head, *gb, (int)P, pixel_offset, env4, E, out4, ctx->num_sms, nl,
+                                        wg, s) != cudaSuccess ||
+              cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            st = RT_ERR_CUDA;
+        }
+        if (st == RT_OK && ms < best) {
+          best = ms;
+          best_nl = nl;
+          best_wg = wg;
+          best_dpt = dpt;
+        }
       }
     }
   }
@@ -496,6 +506,7 @@ rt_status rt_tune(rt_ctx* ctx, const rt_gbuffer* gb, int64_t P, int64_t pixel_of
   if (st != RT_OK) return st;
   ctx->tuned_nl = best_nl;
   ctx->tuned_wg = best_wg;
+  ctx->tuned_dpt = best_dpt;
   if (best_ms) *best_ms = best;
   return RT_OK;
 }
@@ -513,6 +524,19 @@ rt_status rt_set_launch_shape(rt_ctx* ctx, int32_t lights_per_launch, int32_t wa
   if (!(nl == 1 || nl == 2 || nl == 4 || nl == 8) || warpgroups < 2 || warpgroups > 4) return RT_ERR_INVALID_ARG;
   ctx->tuned_nl = nl;
   ctx->tuned_wg = warpgroups;
+  return RT_OK;
+}
+
+rt_status rt_tuned_tile_shape(const rt_ctx* ctx, int32_t* dirs_per_tile) {
+  if (ctx == nullptr || dirs_per_tile == nullptr) return RT_ERR_INVALID_ARG;
+  *dirs_per_tile = ctx->tuned_dpt;
+  return RT_OK;
+}
+
+rt_status rt_set_tile_shape(rt_ctx* ctx, int32_t dirs_per_tile) {
+  if (ctx == nullptr || !(dirs_per_tile == 32 || dirs_per_tile == 64 || dirs_per_tile == 128))
+    return RT_ERR_INVALID_ARG;
+  ctx->tuned_dpt = dirs_per_tile;
   return RT_OK;
 }
 

@@ -124,8 +124,9 @@ constexpr int TM_D = 0, TM_X = 64, TM_H = 96;
 constexpr int SM_W = 0;
 constexpr int WG_FPIX = 0;                   // primary features, bf16 hi parts [34][32]; reused as red[128] float4
 constexpr int WG_FPIX_LO = kFpixLo;          // their bf16 lo parts [34][32]
-constexpr int WG_MISC = 2 * kPixSlots * 64;  // mbarrier (8), then carry[NL] float4 from +16
-constexpr int WG_BYTES = WG_MISC + 256;
+constexpr int WG_MISC = 2 * kPixSlots * 64;  // mbarrier (8), then carry[kCarrySlots][NL] float4 from +16
+constexpr int kCarrySlots = 4;               // pixels of a tile that carry partial sums to the next tile
+constexpr int WG_BYTES = WG_MISC + 16 + kCarrySlots * 8 * 16;
 // hard visibility: a ring of 256 queued shadow rows, the row keys of a tile and per-warp counts
 constexpr int WG_QA = WG_BYTES;              // float4 (w_i, t) [256]
 constexpr int WG_QB = WG_QA + 256 * 16;      // int2 (pixel, i) [256]
@@ -133,7 +134,7 @@ constexpr int WG_KEYS = WG_QB + 256 * 8;     // int [128]
 constexpr int WG_CNT = WG_KEYS + 128 * 4;    // int [4]
 constexpr int WG_BYTES_HARD = WG_CNT + 128;
 constexpr int SM_WG = WBF16_BYTES;
-static_assert(WG_MISC + 16 + 8 * 16 <= WG_BYTES, "warpgroup block overflow");
+static_assert(WG_MISC + 16 + kCarrySlots * 8 * 16 <= WG_BYTES, "warpgroup block overflow");
 static_assert(WG_CNT + 16 <= WG_BYTES_HARD, "warpgroup block overflow (hard visibility)");
 static_assert(128 * 16 <= 2 * kPixSlots * 64 && WG_MISC % 16 == 0 && WG_BYTES_HARD % 16 == 0, "pixel slots");
 
@@ -204,7 +205,7 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
   const long long s_end = p1 * N;
   uint32_t phase = 0;
   int abort = 0;
-  if (t < NL) carry_s[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (t < kCarrySlots * NL) carry_s[t] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // One MMA round trip: barrier with an abort vote, issue by thread 0,
   // commit, bounded wait.  A wait that gives up only raises `abort`; the
@@ -436,15 +437,44 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
         }
     }
   } else {
-    for (long long sbase = p0 * N; sbase < s_end; sbase += 128) {
-      const long long p_first = sbase / N;
-      const int off0 = (int)(sbase - p_first * N);
-      const int nvalid = (int)min(128LL, s_end - sbase);
-      const int npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
+    // Tile order.  dpt = 0: tiles of 128 consecutive samples (pixel-major); a
+    // pixel may start in one tile and end in the next.  dpt = 32 or 64 (the
+    // tile shape of rt_set_tile_shape, N a multiple of it): a tile is
+    // 128 / dpt pixels x dpt directions, and the warpgroup walks the N / dpt
+    // direction chunks of a pixel group before the next group, each pixel's
+    // sum carried across its chunks.  Every (pixel, direction) row computes
+    // the same values in either order, and for N a multiple of 32 the sums are
+    // added in the same order, so the two orders give the same bits.
+    const int dpt = (m.dpt == 32 || m.dpt == 64) && N % m.dpt == 0 && N > m.dpt ? m.dpt : 0;
+    const int gpix = dpt ? 128 / dpt : 0;
+    const int nchunk = dpt ? N / dpt : 1;
+    const long long ntiles = dpt ? (p1 - p0 + gpix - 1) / gpix * nchunk : (s_end - p0 * N + 127) / 128;
+    for (long long tile = 0; tile < ntiles; ++tile) {
+      long long p_first, sbase = 0;
+      int off0 = 0, nvalid, npix, chunk = 0;
+      if (dpt) {
+        chunk = (int)(tile % nchunk);
+        p_first = p0 + tile / nchunk * gpix;
+        npix = (int)min((long long)gpix, p1 - p_first);
+        nvalid = npix * dpt;
+      } else {
+        sbase = p0 * N + 128 * tile;
+        p_first = sbase / N;
+        off0 = (int)(sbase - p_first * N);
+        nvalid = (int)min(128LL, s_end - sbase);
+        npix = (int)((sbase + nvalid - 1) / N - p_first) + 1;
+      }
       const bool valid = t < nvalid;
-      const int local = off0 + (valid ? t : nvalid - 1);
-      const int ps = local / N;
-      const int i = local - ps * N;
+      const int row = valid ? t : nvalid - 1;
+      int ps, i;
+      if (dpt) {
+        ps = row / dpt;
+        i = chunk * dpt + (row - ps * dpt);
+      } else {
+        const int local = off0 + row;
+        ps = local / N;
+        i = local - ps * N;
+      }
       const long long p = p_first + ps;
 
       // (a) primary features of the tile's pixels
@@ -557,28 +587,33 @@ render_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant__ 
           const int ok2 = __shfl_down_sync(0xffffffffu, key, off);
           if (lane + off < 32 && ok2 == key) ce = mk(ce.x + ox, ce.y + oy, ce.z + oz);
         }
+        // pixel slot t's partial sum from the previous tile (read before the barrier that orders it
+        // against this tile's carry writes): slot 0 in the consecutive order, every slot between chunks
+        f3 sum = mk(0.f, 0.f, 0.f);
+        if (t < npix && (dpt ? chunk > 0 : t == 0)) {
+          const float4 cs = carry_s[(dpt ? t : 0) * NL + e];
+          sum = mk(cs.x, cs.y, cs.z);
+        }
         wg_sync(wg);   // fpix reads (first light) or the previous light's sums are done
         red[t] = head ? make_float4(ce.x, ce.y, ce.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
         wg_sync(wg);
         if (t < npix) {
-          const int ra = max(0, t * N - off0);
-          const int rb = min(nvalid, (t + 1) * N - off0);
-          f3 sum = mk(0.f, 0.f, 0.f);
-          if (t == 0) {
-            const float4 cs = carry_s[e];
-            sum = mk(cs.x, cs.y, cs.z);
-          }
+          const int ra = dpt ? t * dpt : max(0, t * N - off0);
+          const int rb = dpt ? ra + dpt : min(nvalid, (t + 1) * N - off0);
           for (int r = ra; r < rb; r = ((r >> 5) + 1) << 5) {
             const float4 h = red[r];
             sum = mk(sum.x + h.x, sum.y + h.y, sum.z + h.z);
           }
-          const bool complete = (p_first + t + 1) * N <= sbase + nvalid;
+          const bool complete = dpt ? chunk == nchunk - 1 : (p_first + t + 1) * N <= sbase + nvalid;
           if (complete) {
             const float sc = kPi / (float)N;
             out[(long long)e * P + p_first + t] = make_float4(sum.x * sc, sum.y * sc, sum.z * sc, 0.0f);
           }
-          if (t == npix - 1)
+          if (dpt) {
+            if (!complete) carry_s[t * NL + e] = make_float4(sum.x, sum.y, sum.z, 0.f);
+          } else if (t == npix - 1) {
             carry_s[e] = complete ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(sum.x, sum.y, sum.z, 0.f);
+          }
         }
       }
       wg_sync(wg);

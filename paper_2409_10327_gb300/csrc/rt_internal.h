@@ -99,6 +99,8 @@ struct ModelDesc {
   const int* guide_c;          // [env_h][1 << gc_shift] cutpoints of each conditional CDF
   int gm_shift, gc_shift;
   int lambert;
+  int dpt;                     // BF16 soft-visibility tile shape: directions of a pixel per 128-row tile (32, 64;
+                               // anything else: tiles of 128 consecutive samples)
   uint64_t seed;
 };
 

@@ -5,7 +5,7 @@ environment maps on a shared geometry pass); the V calls are captured once
 into a CUDA graph and replayed as a single launch.  Timing events recorded
 between the views inside the graph give per-view latencies.  Before capture
 the context's launch shape can be picked by the native autotuner (rt_tune) on
-the first view.
+the first view (or a slice of it).
 """
 from __future__ import annotations
 
@@ -36,9 +36,14 @@ class BatchedServer:
         self.events = []
         self.tuned_ms = None
 
-    def tune(self) -> float:
-        """Pick the launch shape on the first view (rt_tune); returns its time in ms."""
-        self.tuned_ms = self.r.tune(self.gbs[0], self.envs, self.offsets[0])
+    def tune(self, pixels: Optional[int] = None) -> float:
+        """Pick the launch shape (tile shape, lights per launch, warpgroups) with rt_tune on the first
+        view, or on its first `pixels` pixels (the search times 36 shapes twice each); returns the
+        best time in ms."""
+        gb = self.gbs[0]
+        if pixels is not None and pixels < gb["pos"].shape[0]:
+            gb = {k: v[:pixels] for k, v in gb.items()}
+        self.tuned_ms = self.r.tune(gb, self.envs, self.offsets[0])
         return self.tuned_ms
 
     def render_eager(self) -> torch.Tensor:

@@ -57,7 +57,7 @@ def test_tuner_picks_a_shape_and_reproduces_it(lib):
     r = helpers.renderer_for(cfg, sc)
     best = r.tune(gb, denv)
     nl, wg = r.launch_shape()
-    assert best > 0 and nl in (1, 2, 4, 8) and wg in (2, 3, 4)
+    assert best > 0 and nl in (1, 2, 4, 8) and wg in (2, 3, 4) and r.tile_shape() in (32, 64, 128)
     tuned = r.render_frame_multi(gb, denv).cpu().numpy()
     r.set_launch_shape(1, 2)
     ref = r.render_frame_multi(gb, denv).cpu().numpy()
@@ -118,3 +118,30 @@ def test_serve1080_full_size_multi_light_sampled(lib):
         sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, rel=helpers.BF16_JITTER, draws=helpers.BF16_SENS_DRAWS, mlp=True)
         ok, stats = helpers.bf16_parity(out[e, rows, :3], ref, sens)
         assert ok, (e, r.launch_shape(), stats)
+
+
+@pytest.mark.parametrize("n_dirs,P", [(64, 37), (128, 150), (256, 21), (48, 40)])
+def test_tile_shapes_give_the_same_bits(lib, n_dirs, P):
+    # 32 / 64 directions per tile (128 / d pixels per tile, the direction chunks of a pixel group walked
+    # in order) against tiles of 128 consecutive samples; 48 directions: no chunked shape applies
+    cfg = helpers.small_cfg(n_dirs=n_dirs, m_dirs=4, precision="bf16")
+    sc = scenegen.make_scene(cfg, 3, bias_scale=0.1)
+    gb = helpers.to_cuda(scenegen.make_gbuffer(P, 8))
+    denv = torch.from_numpy(_envs(cfg, 4)).cuda()
+    r = helpers.renderer_for(cfg, sc)
+    assert r.tile_shape() == 128
+    for nl, wg in ((1, 4), (4, 2)):
+        r.set_launch_shape(nl, wg)
+        outs = {}
+        for d in (128, 64, 32):
+            r.set_tile_shape(d)
+            outs[d] = (r.render_frame(gb, pixel_offset=5).cpu().numpy(),
+                       r.render_frame_multi(gb, denv, pixel_offset=5).cpu().numpy())
+        for d in (64, 32):
+            np.testing.assert_array_equal(outs[d][0], outs[128][0])
+            np.testing.assert_array_equal(outs[d][1], outs[128][1])
+    assert r.check() == 0
+    for bad in (0, 16, 96, 256):
+        with pytest.raises(lib.RtError) as e:
+            r.set_tile_shape(bad)
+        assert e.value.status == lib.RT_ERR_INVALID_ARG
