@@ -269,8 +269,8 @@ def _time_frames(renderers, gbs, out, steps, warmup, barrier, clocks=None):
 # reports null.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_frame800.txt")
 KERNEL_SOURCES = {
-    "bf16": ["render_bf16.cu", "tc_common.cuh", "fast_math.cuh", "mis.cuh", "mbarrier.cuh", "device_common.cuh",
-             "rt_internal.h"],
+    "bf16": ["render_bf16.cu", "render_bf16_kernel.cuh", "tc_common.cuh", "fast_math.cuh", "mis.cuh", "mbarrier.cuh",
+             "device_common.cuh", "rt_internal.h"],
     "fp32": ["render_fp32.cu", "warp_gemm.cuh", "mis.cuh", "device_common.cuh", "rt_internal.h"],
 }
 

@@ -132,8 +132,11 @@ cudaError_t launch_sample(const ModelDesc& m, const float4* normal, int P, int l
 cudaError_t launch_shade(const ModelDesc& m, const rt_gbuffer& pts, int P, int level, long long offset,
                          const float* vis, const float4* lin, float4* out, cudaStream_t s);
 cudaError_t launch_repack_bf16(const float* wpack, uint8_t* wbf16, cudaStream_t s);
-cudaError_t launch_render_bf16(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
-                               long long offset, float4* out, int num_sms, cudaStream_t s);
+// the direction-chunk tile shapes (m.dpt 32 / 64), soft visibility, one launch of nl lights
+cudaError_t prepare_render_bf16_chunked();
+cudaError_t launch_render_bf16_chunked(int nl, int wg, const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb,
+                                       int P, long long offset, const float4* envs, float4* out, int num_sms,
+                                       cudaStream_t s);
 cudaError_t launch_render_bf16_lights(const ModelDesc& m, const HeadParams& hp, const rt_gbuffer& gb, int P,
                                       long long offset, const float4* envs, int E, float4* out, int num_sms,
                                       int max_nl, int wg, cudaStream_t s);
