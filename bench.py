@@ -615,6 +615,10 @@ def run_ours(args, cfg):
     main_modes = {"visibility": binding.RT_VIS_HARD if args.visibility == "hard" else binding.RT_VIS_SOFT,
                   "sampling": binding.RT_SAMPLE_MIS if args.sampling == "mis" else binding.RT_SAMPLE_COSINE}
     renderers, gbs = _setup(cfg, rank, **main_modes)
+    if cfg.precision == "bf16":
+        for r in renderers:   # the frame kernel's launch shape (single light)
+            r.set_launch_shape(r.launch_shape()[0], args.warpgroups)
+            r.set_tile_shape(args.dirs_per_tile)
     out = torch.empty(cfg.n_pixels, 4, device="cuda")
     total_ms, launch_ms, clk = _time_frames(renderers, gbs, out, args.steps, args.warmup, barrier,
                                             ClockSampler(local))
@@ -765,7 +769,8 @@ def run_ours(args, cfg):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if cfg.precision == "fp32" else "bf16",
             "data": "synthetic",
             "config": {"workload": workload_name(cfg), "l2": L2_NOTE, "scenes_per_rank": 4,
-                       "visibility": args.visibility, "sampling": args.sampling},
+                       "visibility": args.visibility, "sampling": args.sampling,
+                       "warpgroups": args.warpgroups, "dirs_per_tile": args.dirs_per_tile},
             "roofline": _roofline(cfg, launch_ms, peaks, probes), "cpu_baseline": cpu, "parity": parity,
             "probes": probes, "serve": srv,
             "e2e": {"value": world * cfg.samples * args.steps / (e2e_ms / 1e3), "unit": UNIT,
@@ -885,6 +890,10 @@ def main():
                     help="skip the backward's FP64 gradient check (part of the cpu_baseline leg)")
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--lights", type=int, default=8)
+    ap.add_argument("--warpgroups", type=int, choices=[2, 3, 4], default=4,
+                    help="BF16 frame kernel: warpgroups per CTA")
+    ap.add_argument("--dirs-per-tile", type=int, choices=[32, 64, 128], default=128,
+                    help="BF16 frame kernel: directions of a pixel per 128-row tile (rt_set_tile_shape)")
     ap.add_argument("--pixels", type=int, default=0,
                     help="render only the first P pixel rows of each frame (a smaller case for profilers)")
     args = ap.parse_args()
