@@ -146,3 +146,30 @@ def test_bf16_hard_full_size_frame_sampled(lib):
     assert np.isfinite(out).all()
     rows = scenegen.subset_permutation(cfg.n_pixels, 256, seed=0)
     _bf16_hard_check(cfg, sc, gb, out, rows=rows, psnr=False)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_hard_frame_against_fp64_decisions(lib, precision):
+    # The parity tests above take the decisions in the kernel's arithmetic (with a flip allowance).
+    # This one reports what the decisions themselves change: the oracle's frame with FP64 decisions
+    # against the same frame with decisions in the kernel's arithmetic (pixels touched by a flipped
+    # decision, and the frame L1 of the difference), and the GPU frame against both.
+    cfg = scenegen.CONFIGS["tiny64"] if precision == "fp32" else _bf16(scenegen.CONFIGS["tiny64"])
+    sc, gb = helpers.scene_arrays(cfg, 0, bias=0.1)
+    out = _render(cfg, sc, gb, visibility=HARD)[:, :3]
+    prm = helpers.oracle_params(sc)
+    ref64 = orender.render(gb, prm, helpers.oracle_options(cfg, hard_vis=True, decision_arith="fp64"))
+    refk = orender.render(gb, prm, helpers.oracle_options(cfg, hard_vis=True, decision_arith=precision))
+    ref64, refk = np.asarray(ref64), np.asarray(refk)
+    norm = np.abs(ref64).sum()
+    touched = np.abs(refk - ref64).max(-1) > 1e-12 * np.maximum(np.abs(ref64).max(-1), 1e-300)
+    stats = {"pixels": int(ref64.shape[0]), "pixels_touched_by_flips": int(touched.sum()),
+             "flip_effect_frame_l1": float(np.abs(refk - ref64).sum() / norm),
+             "gpu_vs_fp64_decisions_l1": float(np.abs(out - ref64).sum() / norm),
+             "gpu_vs_kernel_decisions_l1": float(np.abs(out - refk).sum() / norm)}
+    print(precision, stats)
+    # flips are rare and small next to the frame; the GPU frame is closer to the kernel-arithmetic
+    # decisions than to the FP64 ones wherever they differ
+    assert stats["pixels_touched_by_flips"] <= 0.1 * stats["pixels"], stats
+    assert stats["flip_effect_frame_l1"] <= 1e-2, stats
+    assert stats["gpu_vs_kernel_decisions_l1"] <= stats["gpu_vs_fp64_decisions_l1"] + 1e-9, stats
