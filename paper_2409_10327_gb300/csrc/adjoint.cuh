@@ -186,68 +186,6 @@ __device__ __forceinline__ void encode_level_bwd(const GridDesc& g, int l, f3 x,
   }
 }
 
-// The same adjoint for the lanes `act` of a warp that all process level l,
-// each at its own point (the secondary points x' of a chunk's directions, or
-// the points of a B tile).  Lanes whose corner c falls on the same table row
-// (common on the coarse levels, where a pixel's directions share cells) are
-// summed inside the warp by a shuffle tree over their ranks among that row's
-// lanes, so the sum has a fixed order, and the row receives one float2
-// reduction instead of one per lane.  Where no row repeats (the usual case on
-// the fine hashed levels) every lane adds its own contribution.
-__device__ __forceinline__ void encode_level_bwd_warp(const GridDesc& g, int l, f3 x, float df0, float df1,
-                                                      float* __restrict__ g_table, f3* dx, unsigned act) {
-  const int res = g.res[l];
-  const unsigned lane = threadIdx.x & 31u;
-  uint32_t ix, iy, iz;
-  float wx, wy, wz;
-  grid_cell_exact(x.x, res, ix, wx);
-  grid_cell_exact(x.y, res, iy, wy);
-  grid_cell_exact(x.z, res, iz, wz);
-  const size_t base = (size_t)l << g.log2T;
-  const int dense = g.dense[l];
-  float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
-    const uint32_t row = corner_row(ix + ox, iy + oy, iz + oz, res, dense, g.mask);
-    const float ax = ox ? wx : 1.0f - wx, ay = oy ? wy : 1.0f - wy, az = oz ? wz : 1.0f - wz;
-    const float w = ax * ay * az;
-    float v0 = w * df0, v1 = w * df1;
-    const unsigned grp = __match_any_sync(act, row);
-    bool lead = true;
-    if (__any_sync(act, grp != (1u << lane))) {
-      const unsigned rank = __popc(grp & ((1u << lane) - 1u));
-#pragma unroll
-      for (unsigned s = 1; s < 32; s <<= 1) {
-        const unsigned src = __fns(grp, lane, (int)s + 1);   // the lane s places after this one in its row
-        const bool take = (rank % (2 * s)) == 0 && src < 32u;
-        const float o0 = __shfl_sync(act, v0, take ? src : lane);
-        const float o1 = __shfl_sync(act, v1, take ? src : lane);
-        if (take) {
-          v0 += o0;
-          v1 += o1;
-        }
-      }
-      lead = rank == 0;
-    }
-    if (lead) atomicAdd(reinterpret_cast<float2*>(g_table) + base + row, make_float2(v0, v1));
-    if (dx != nullptr) {
-      const float2 e = table_entry(g, base + row);
-      const float de = e.x * df0 + e.y * df1;
-      gx += de * (ox ? 1.0f : -1.0f) * ay * az;
-      gy += de * (oy ? 1.0f : -1.0f) * ax * az;
-      gz += de * (oz ? 1.0f : -1.0f) * ax * ay;
-    }
-  }
-  if (dx != nullptr) {
-    const float s = 0.5f * (float)res;
-    const float ux = x.x * 0.5f + 0.5f, uy = x.y * 0.5f + 0.5f, uz = x.z * 0.5f + 0.5f;
-    dx->x += (ux >= 0.0f && ux <= 1.0f) ? gx * s : 0.0f;
-    dx->y += (uy >= 0.0f && uy <= 1.0f) ? gy * s : 0.0f;
-    dx->z += (uz >= 0.0f && uz <= 1.0f) ? gz * s : 0.0f;
-  }
-}
-
 // Bitonic sort of one 32-bit key per lane across the warp, ascending with the
 // lane index.  All 32 lanes take part.
 __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key) {
@@ -290,8 +228,10 @@ __device__ __forceinline__ uint32_t morton_cell8(float u) {
 // bounded by the run (a fixed order of additions) and reaches the table as one
 // float2 reduction; a row whose points are not consecutive receives one
 // reduction per run.  Levels without runs cost one ballot per corner over the
-// plain scatter.  Returns dLoss/dx of this lane's own point; scratch is 512
-// bytes of the warp's shared memory (the points' dx on their way back).
+// plain scatter.  With WANT_DX, returns dLoss/dx of this lane's own point, and
+// scratch is 512 bytes of the warp's shared memory (the points' dx on their way
+// back); without it, returns zero and scratch is unused (may be null).
+template <bool WANT_DX = true>
 __device__ __forceinline__ f3 encode_bwd_sorted(const GridDesc& g, f3 x, const uint32_t (&df)[32], bool valid,
                                                 float* __restrict__ g_table, float4* scratch) {
   const unsigned lane = threadIdx.x & 31u;
@@ -352,7 +292,7 @@ __device__ __forceinline__ f3 encode_bwd_sorted(const GridDesc& g, f3 x, const u
         }
       }
       if (head && live) atomicAdd(reinterpret_cast<float2*>(g_table) + base + row, make_float2(v0, v1));
-      if (live) {
+      if (WANT_DX && live) {
         const float2 e = table_entry(g, base + row);
         const float de = e.x * df0 + e.y * df1;
         gx += de * (ox ? 1.0f : -1.0f) * ay * az;
@@ -360,13 +300,16 @@ __device__ __forceinline__ f3 encode_bwd_sorted(const GridDesc& g, f3 x, const u
         gz += de * (oz ? 1.0f : -1.0f) * ax * ay;
       }
     }
-    // dg/dx = N_l / 2 inside the box, 0 on a clamped axis
-    const float s = 0.5f * (float)res;
-    const float ux = xs.x * 0.5f + 0.5f, uy = xs.y * 0.5f + 0.5f, uz = xs.z * 0.5f + 0.5f;
-    dx.x += (ux >= 0.0f && ux <= 1.0f) ? gx * s : 0.0f;
-    dx.y += (uy >= 0.0f && uy <= 1.0f) ? gy * s : 0.0f;
-    dx.z += (uz >= 0.0f && uz <= 1.0f) ? gz * s : 0.0f;
+    if (WANT_DX) {
+      // dg/dx = N_l / 2 inside the box, 0 on a clamped axis
+      const float s = 0.5f * (float)res;
+      const float ux = xs.x * 0.5f + 0.5f, uy = xs.y * 0.5f + 0.5f, uz = xs.z * 0.5f + 0.5f;
+      dx.x += (ux >= 0.0f && ux <= 1.0f) ? gx * s : 0.0f;
+      dx.y += (uy >= 0.0f && uy <= 1.0f) ? gy * s : 0.0f;
+      dx.z += (uz >= 0.0f && uz <= 1.0f) ? gz * s : 0.0f;
+    }
   }
+  if (!WANT_DX) return dx;
   // back to the lane that owns the point
   scratch[src] = make_float4(dx.x, dx.y, dx.z, 0.0f);
   __syncwarp();

@@ -289,12 +289,13 @@ distill_fp32_kernel(ModelDesc m, const float4* __restrict__ pos4, const float4* 
 #pragma unroll
     for (int k = 0; k < 32; ++k) dF[k] = 0.0f;
     bwd_input(H1, sw + OFF_BW1, lf, dF, lane);
-    const unsigned act = __ballot_sync(0xffffffffu, vp);
-    if (vp) {
-      const f3 x = xyz(pos4[p]);
+    {
+      // segmented scatter over the warp's points (Morton order, runs of equal rows summed first)
+      uint32_t dbits[32];
 #pragma unroll
-      for (int l = 0; l < kMaxLevels; ++l)
-        if (l < levels) encode_level_bwd_warp(m.grid, l, x, dF[2 * l], dF[2 * l + 1], g_table, nullptr, act);
+      for (int k = 0; k < 32; ++k) dbits[k] = __float_as_uint(dF[k]);
+      const f3 x = vp ? xyz(pos4[p]) : mk(0.f, 0.f, 0.f);
+      (void)encode_bwd_sorted<false>(m.grid, x, dbits, vp, g_table, nullptr);
     }
     __syncwarp();
   }

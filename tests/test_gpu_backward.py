@@ -186,8 +186,9 @@ def test_autograd_directional_finite_difference(lib):
 
 
 def test_backward_run_to_run_variation_is_rounding_level(lib):
-    # Lanes of a warp that hit the same table row are summed in a fixed order before one
-    # float2 reduction; reductions from different warps still land in a varying order, so
+    # A warp's points are sorted into Morton order and each run of lanes on one table row is summed
+    # in a fixed order before one float2 reduction; reductions from different warps still land in a
+    # varying order, so
     # two identical calls may differ in the last bits of the table gradient, and only there.
     cfg = helpers.small_cfg(n_dirs=32, m_dirs=4, levels=6, log2_T=12, max_res=128)
     sc, gb, up, ref = _case(cfg, 48)
