@@ -64,7 +64,8 @@ constexpr int WB_SC = 32768;                          // [128 rows][64] bf16: re
 constexpr int WB_SD = 49152;                          // [128 rows][16] bf16 (32-byte swizzle): dZ3, zero-padded
 constexpr int WB_FPIX = 53248;                        // kPixSlots x 64 B hi, then lo; later float [kPixSlots][32]
 constexpr int WB_BAR = WB_FPIX + 2 * kFpixLo;
-constexpr int WB_BYTES = ((WB_BAR + 16 + 1023) / 1024) * 1024;
+constexpr int WB_JAC = ((WB_BAR + 16 + 127) / 128) * 128;   // uint32 (half2) [3 L][128 rows]: d f' / d w at x'
+constexpr int WB_BYTES = ((WB_JAC + 3 * kMaxLevels * 128 * 4 + 1023) / 1024) * 1024;
 constexpr int BS_TSLOT = BS_WGB + kBWG * WB_BYTES;
 constexpr size_t kBSmem16 = (size_t)BS_TSLOT + 16 + 1024;
 static_assert(kPixSlots * 32 * 4 <= 2 * kFpixLo, "per-pixel df sums fit the feature slots");
@@ -214,6 +215,7 @@ backward_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant_
   uint8_t* fpix = wgb + WB_FPIX;
   float* dfs = reinterpret_cast<float*>(wgb + WB_FPIX);   // [kPixSlots][32] after the features are consumed
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgb + WB_BAR);
+  uint32_t* jac = reinterpret_cast<uint32_t*>(wgb + WB_JAC);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + BS_TSLOT);
 
   // ---- CTA set-up: weights (the forward's image), TMEM, barriers
@@ -485,8 +487,8 @@ backward_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant_
     const float tdep = m.near_t + (m.far_t - m.near_t) * fminf(sp, 1.0f);
     const f3 x2 = x + wi * tdep;
 
-    // (d) f' = H(x') into X; (b) B(f')
-    encode_point_tmem(m.grid, x2, X_w);
+    // (d) f' = H(x') into X, with its derivative along the cell fractions for dLoss/dx'; (b) B(f')
+    encode_point_tmem<true>(m.grid, x2, X_w, jac, t);
     store_bias_cols_tmem(X_w);
     if (!run_mma([&] { mma_brdf_layer1(D_t, X_t, W_s + OFFB_BW1); })) break;
     epilogue_hidden(D_w, H_w);
@@ -562,14 +564,39 @@ backward_bf16_kernel(const __grid_constant__ ModelDesc m, const __grid_constant_
         break;
     }
 
-    // encode adjoint at x': table gradients (segmented scatter over the warp's points in Morton order)
-    // and dLoss/dx'; the warp's slice of SA (free between round trips) carries dx' back to its lane
-    f3 dx2;
+    // encode adjoint at x': table gradients (segmented scatter over the warp's points in Morton order),
+    // and dLoss/dx' = sum over levels of (N_l / 2) (d f'_l / d w) . dLoss/df'_l from the cached derivative
+    f3 dx2 = mk(0.f, 0.f, 0.f);
     {
       uint32_t r[32];
       tmem_ld32(F_w, r);
       tmem_ld_wait();
-      dx2 = encode_bwd_sorted(m.grid, x2, r, valid, g_table, reinterpret_cast<float4*>(slice));
+      (void)encode_bwd_sorted<false>(m.grid, x2, r, valid, g_table, nullptr);
+      if (valid) {
+#pragma unroll 1
+        for (int l = 0; l < m.grid.levels; ++l) {
+          float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (k == l) {
+              d0 = __uint_as_float(r[2 * k]);
+              d1 = __uint_as_float(r[2 * k + 1]);
+            }
+          const float s = (float)m.grid.res[l];   // N_l / 2 times the halving of the stored derivative
+          float g3[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const uint32_t wv = jac[(3 * l + a) * 128 + t];
+            const float2 j = __half22float2(*reinterpret_cast<const __half2*>(&wv));
+            g3[a] = s * fmaf(j.x, d0, j.y * d1);
+          }
+          dx2 = mk(dx2.x + g3[0], dx2.y + g3[1], dx2.z + g3[2]);
+        }
+        // dg/dx = N_l / 2 inside the box, 0 on a clamped axis
+        const float ux = x2.x * 0.5f + 0.5f, uy = x2.y * 0.5f + 0.5f, uz = x2.z * 0.5f + 0.5f;
+        dx2 = mk((ux >= 0.0f && ux <= 1.0f) ? dx2.x : 0.0f, (uy >= 0.0f && uy <= 1.0f) ? dx2.y : 0.0f,
+                 (uz >= 0.0f && uz <= 1.0f) ? dx2.z : 0.0f);
+      }
     }
     const float dt = dot(dx2, wi);
     float dzp[2];

@@ -269,7 +269,14 @@ __device__ __forceinline__ float head_vis(uint32_t taddr, const float* w, float 
 // dense level with an even row), which removes about a quarter of the
 // gathers.  (Aligned 16-byte loads, which pair the corners three times in
 // four, measured 5 % slower.)
-__device__ __forceinline__ void encode_point_tmem(const GridDesc& g, f3 x, uint32_t x_taddr) {
+// With JAC, also the interpolation's derivative along each axis, per level: for
+// features (f0, f1) of level l, d f / d w_a (w_a the cell fraction on axis a),
+// halved and stored as a half2 in jac[(3 l + a) * 128 + row] (column-major over
+// the tile's 128 rows; halved so that it always fits half precision when the
+// table is FP16).  The adjoint's dLoss/dx' then needs no second gather.
+template <bool JAC = false>
+__device__ __forceinline__ void encode_point_tmem(const GridDesc& g, f3 x, uint32_t x_taddr, uint32_t* jac = nullptr,
+                                                  int row = 0) {
 #pragma unroll 1
   for (int it = 0; it < kMaxLevels / 4; ++it) {
     uint32_t fq[4];
@@ -305,6 +312,25 @@ __device__ __forceinline__ void encode_point_tmem(const GridDesc& g, f3 x, uint3
           const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[c]));
           f0 = fmaf(wt, e.x, f0);
           f1 = fmaf(wt, e.y, f1);
+        }
+        if constexpr (JAC) {
+          float2 j[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;   // corner c = v[c] (x fastest)
+            const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&v[c]));
+            const float ax = cx ? w[0] : 1.0f - w[0], ay = cy ? w[1] : 1.0f - w[1], az = cz ? w[2] : 1.0f - w[2];
+            const float gx = (cx ? 0.5f : -0.5f) * ay * az, gy = (cy ? 0.5f : -0.5f) * ax * az,
+                        gz = (cz ? 0.5f : -0.5f) * ax * ay;
+            j[0] = make_float2(fmaf(gx, e.x, j[0].x), fmaf(gx, e.y, j[0].y));
+            j[1] = make_float2(fmaf(gy, e.x, j[1].x), fmaf(gy, e.y, j[1].y));
+            j[2] = make_float2(fmaf(gz, e.x, j[2].x), fmaf(gz, e.y, j[2].y));
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const __half2 h = __floats2half2_rn(j[a].x, j[a].y);
+            jac[(3 * l + a) * 128 + row] = *reinterpret_cast<const uint32_t*>(&h);
+          }
         }
       }
       fq[b] = pack_bf16(f0, f1);
