@@ -22,10 +22,12 @@
 //      against an all-ones tile, dW3 is relu(pre2)^T dZ3 and db3 a warp sum;
 //   3. recomputes B and back-propagates it (dLoss/d(a', r', n') from step 2)
 //      the same way into df';
-//   4. scatters df' into the table at x' (warp-segmented float2 reductions)
-//      and takes dLoss/dx' through the trilinear weights, turns it into dt
-//      and dz1, and back-propagates the primary I (recomputed in split
-//      precision, back-propagated in bf16) into its weights and into df;
+//   4. scatters df' into the table at x' (the warp's points in Morton order,
+//      runs of equal rows summed before one float2 reduction each), takes
+//      dLoss/dx' from the interpolation derivative that step 1's encode of
+//      x' cached in shared memory, turns it into dt and dz1, and back-
+//      propagates the primary I (recomputed in split precision, back-
+//      propagated in bf16) into its weights and into df;
 //   5. sums df over the rows of each pixel of the tile and scatters it into
 //      the table at x (the encode adjoint is linear, so a pixel split over
 //      tiles scatters each part).
