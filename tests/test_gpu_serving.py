@@ -88,12 +88,16 @@ def test_multi_light_bf16_against_oracle(lib):
     envs = _envs(cfg, 3)
     r = helpers.renderer_for(cfg, sc)
     out = r.render_frame_multi(helpers.to_cuda(gb), torch.from_numpy(envs).cuda()).cpu().numpy()
+    # every light on a seeded quarter of the frame (the whole single-light frame is checked in
+    # test_gpu_render_bf16.py; multi- and single-light renders are compared in full above)
+    rows = np.sort(scenegen.subset_permutation(cfg.n_pixels, cfg.n_pixels // 4, seed=2))
     for e in range(3):
         prm = orender.Params.from_arrays(sc.table, sc.brdf, sc.irt, envs[e])
         opt = helpers.oracle_options(cfg)
-        ref = orender.render(gb, prm, opt)
-        sens = orender.float32_sensitivity(gb, prm, opt, rel=helpers.BF16_JITTER, draws=helpers.BF16_SENS_DRAWS, mlp=True)
-        ok, stats = helpers.bf16_parity(out[e, :, :3], ref, sens)
+        ref = orender.render(gb, prm, opt, rows=rows)
+        sens = orender.float32_sensitivity(gb, prm, opt, rows=rows, rel=helpers.BF16_JITTER,
+                                           draws=helpers.BF16_SENS_DRAWS, mlp=True)
+        ok, stats = helpers.bf16_parity(out[e, rows, :3], ref, sens)
         assert ok and stats["psnr_db"] >= helpers.BF16_PSNR_MIN, (e, stats)
 
 
@@ -107,7 +111,7 @@ def test_serve1080_full_size_multi_light_sampled(lib):
     r = helpers.renderer_for(cfg, sc)
     dgb = helpers.to_cuda(gb)
     denv = torch.from_numpy(envs).cuda()
-    r.tune(dgb, denv)
+    r.tune({k: v[:cfg.n_pixels // 8] for k, v in dgb.items()}, denv)   # as the serving bench: the first eighth
     out = r.render_frame_multi(dgb, denv).cpu().numpy()
     assert np.isfinite(out).all() and np.all(out[..., 3] == 0)
     rows = scenegen.subset_permutation(cfg.n_pixels, 48, seed=4)
